@@ -1,0 +1,83 @@
+/*
+ * Oracle for one multiparticle-collision-dynamics (MPC) step: plain, single-threaded,
+ * FP64 C.  TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library; the product path never does.
+ * It shares no code with the CUDA implementation: both follow the same written
+ * contract (fixed-point positions, Philox keying), each in its own code.
+ *
+ * Paper: Westphal, Goh, Winkler, Gompper, "HTMPC", arXiv 2406.15236,
+ *   Sec. II Eq. (1)  streaming,            Eq. (2) SRD collision,
+ *   Sec. II Eqs.(3)-(4) SRD+a (angular-momentum conservation),
+ *   Sec. II Eqs.(5)-(7) Maxwell-Boltzmann-scaling thermostat,
+ *   Sec. II "Boundary conditions" (bounce-back walls, phantom particles),
+ *   Sec. II "External fields" (gravity), Sec. III.A.3 permanent reorder.
+ * MPC-AT+a follows the reference the paper cites for angular-momentum-conserving
+ * MPC (Noguchi, Kikuchi, Gompper 2007).
+ */
+#ifndef MPC_ORACLE_H
+#define MPC_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_SRD = 0, ORC_AT_A = 1, ORC_SRD_A = 2 };
+
+typedef struct {
+  int32_t L[3];          /* box edge in collision cells (a = 1) */
+  double n_c;            /* mean particles per cell */
+  double h;              /* time step */
+  double alpha_deg;      /* SRD rotation angle */
+  double kT;             /* thermal energy */
+  double m;              /* particle mass */
+  int32_t variant;       /* ORC_SRD / ORC_AT_A / ORC_SRD_A */
+  int32_t thermostat;    /* 1: MBS after SRD */
+  int32_t walls_z;       /* 1: no-slip bounce-back walls at z = 0 and z = Lz */
+  double g[3];           /* body-force acceleration */
+  uint64_t seed;
+  uint32_t box;          /* fourth Philox counter word */
+} orc_params;
+
+/* per-cell flags written by orc_step */
+enum {
+  ORC_FLAG_MBS_NEAR_TIE = 1,   /* a Marsaglia-Tsang decision was within 1e-5 of its threshold */
+  ORC_FLAG_POISSON_NEAR_TIE = 2,
+  ORC_FLAG_ILL_CONDITIONED = 4, /* angular-momentum solve with cond(J) > 1e3 */
+  ORC_FLAG_DEGENERATE = 8       /* n >= 3 but det(J) <= 0: omega set to zero */
+};
+
+/* observables slots (orc_step obs_out, 16 doubles) */
+enum {
+  ORC_OBS_PX = 0, ORC_OBS_PY, ORC_OBS_PZ, ORC_OBS_EKIN, ORC_OBS_TEMP,
+  ORC_OBS_SKIN_XY, ORC_OBS_SKIN_YZ, ORC_OBS_SKIN_ZX,
+  ORC_OBS_SCOL_XY, ORC_OBS_SCOL_YX, ORC_OBS_SCOL_YZ, ORC_OBS_SCOL_ZY,
+  ORC_OBS_SCOL_ZX, ORC_OBS_SCOL_XZ, ORC_OBS_COUNT = 16
+};
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+int orc_fixed_bits(const orc_params* p);
+int64_t orc_num_particles(const orc_params* p);
+int64_t orc_num_cells(const orc_params* p);
+void orc_shift(const orc_params* p, int64_t step, uint32_t S[3]);
+
+int orc_init(const orc_params* p, int64_t N, uint32_t* X, double* V, uint32_t* id);
+
+int orc_step(const orc_params* p, int64_t N, uint32_t* X, double* V, const uint32_t* id,
+             int64_t step, uint32_t* cell_out, uint32_t* count_out, double* vpre_out,
+             double* obs_out, uint8_t* cell_flags);
+
+/* building blocks exposed for the pin tests */
+int orc_cell_of(const orc_params* p, const uint32_t x[3], const uint32_t S[3],
+                uint32_t* cell, double rho[3]);
+void orc_srd_axis(const orc_params* p, int64_t step, uint32_t cell, double axis[3]);
+void orc_rotate(const double axis[3], double alpha_rad, const double v[3], double out[3]);
+void orc_stream_one(const orc_params* p, uint32_t x[3], double v[3]);
+void orc_sample_normal(uint64_t seed, int64_t n, double* out);
+void orc_sample_gamma(uint64_t seed, double shape, int64_t n, double* out);
+void orc_sample_poisson(uint64_t seed, double lambda, int64_t n, int32_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
