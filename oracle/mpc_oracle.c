@@ -71,8 +71,9 @@ static void draw(const orc_params* p, uint32_t c0, uint32_t c1, uint32_t tag, ui
   orc_philox4x32_10(ctr, key, out);
 }
 
-/* uniform in (0,1): 24 random bits plus half an ulp; exact in float and double */
-static double uniform01(uint32_t r) { return ((double)(r >> 8) + 0.5) * (1.0 / 16777216.0); }
+/* uniform in (0,1): the top 23 random bits plus half of their ulp, (2k+1) / 2^24 with
+ * k < 2^23 -- a 24-bit odd numerator, so the value is exact in float and double */
+static double uniform01(uint32_t r) { return ((double)(r >> 9) + 0.5) * (1.0 / 8388608.0); }
 
 /* Box-Muller: two uniforms -> two independent standard normals */
 static void box_muller(double u0, double u1, double* z0, double* z1) {
