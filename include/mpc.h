@@ -1,0 +1,177 @@
+/*
+ * mpc.h -- C ABI of the GB300 multiparticle-collision-dynamics (MPC) step library.
+ *
+ * One MPC time step (Westphal, Goh, Winkler, Gompper, arXiv 2406.15236, Sec. II):
+ *   streaming              r_i <- r_i + h v_i                       (Eq. 1)
+ *   boundary conditions    periodic, or bounce-back walls at z = 0, Lz with phantom
+ *                          particles in the wall part of cut cells  (Sec. II, "Boundary
+ *                          conditions")
+ *   body force             v_i <- v_i + g h before streaming        (Sec. II, "External fields")
+ *   random lattice shift   one uniform vector in [0, a)^3 per step  (Sec. II, after Eq. 2)
+ *   collision per cell     SRD rotation v_i <- v_cm + D(alpha)(v_i - v_cm)   (Eq. 2)
+ *                          or MPC-AT+a (angular-momentum-conserving Andersen-thermostat
+ *                          MPC of the reference cited with Eqs. 3-4)
+ *   thermostat             Maxwell-Boltzmann scaling, kappa = sqrt(2E_k / sum m v_ic^2),
+ *                          E_k ~ Gamma(3(N_c-1)/2, kT)              (Eqs. 5-7)
+ *   reorder                particles are binned by collision cell every step
+ *                          (Sec. III.B.3, permanent exchange / spatial reorder)
+ *
+ * State contract (shared by every entry point):
+ *   - Positions are 32-bit unsigned fixed point per axis with F fraction bits per cell
+ *     length a = 1, F = 31 - ceil(log2(max L)); X in [0, L << F).
+ *   - Velocities are float32.  Arrays are structure-of-arrays: X = {x[N], y[N], z[N]},
+ *     V = {vx[N], vy[N], vz[N]}; id[N] is a persistent particle tag (Sec. III.C,
+ *     "Fluid Particle ID") that keys per-particle random draws.
+ *   - Random numbers are Philox4x32-10 keyed by (seed) with counter
+ *     (index, step, tag << 24 | sub-draw, box_id), so results do not depend on the
+ *     order of particles in memory.
+ *
+ * Errors: every call returns an mpc_status; nothing aborts.  mpc_last_error() gives the
+ * text of the last error on a handle (or of the last failed mpc_create when NULL).
+ * Threading: a handle may be used by one host thread at a time.
+ * Streams: work is enqueued on the CUDA stream given to mpc_create (a cudaStream_t
+ * passed as void*, NULL for the legacy default stream); calls that return data to
+ * the host synchronise that stream.
+ */
+#ifndef MPC_H
+#define MPC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpc_s* mpc_handle;
+
+typedef enum {
+  MPC_SRD = 0,    /* stochastic rotation dynamics, Eq. (2) */
+  MPC_AT_A = 1,   /* Andersen-thermostat MPC with angular-momentum conservation */
+  MPC_SRD_A = 2   /* SRD with angular-momentum conservation, Eqs. (3)-(4) */
+} mpc_variant;
+
+typedef enum {
+  MPC_OK = 0,
+  MPC_EINVAL = 1,    /* invalid argument or parameter combination */
+  MPC_ENOMEM = 2,    /* device or host allocation failed */
+  MPC_ECUDA = 3,     /* a CUDA call failed (text in mpc_last_error) */
+  MPC_ETIMEOUT = 4,  /* a bounded device-side wait gave up */
+  MPC_ESTATE = 5     /* state inconsistent (e.g. a particle outside the box) */
+} mpc_status;
+
+enum {
+  MPC_FLAG_OBSERVABLES = 1u,  /* accumulate observables inside every step */
+  MPC_FLAG_DEBUG_CELLS = 2u   /* keep each particle's collision cell and per-cell counts */
+};
+
+typedef struct {
+  int32_t L[3];          /* box edge lengths in collision cells, each in [2, 1024] */
+  double a;              /* collision-cell size; must be 1.0 (lengths are in units of a) */
+  double n_c;            /* mean particles per cell <N_c>; N = round(Lx Ly Lz n_c) */
+  double h;              /* time step, > 0 */
+  double alpha_deg;      /* SRD rotation angle in degrees (SRD, SRD+a) */
+  double kT;             /* thermal energy k_B T, > 0 */
+  double m;              /* particle mass, > 0 */
+  int32_t variant;       /* mpc_variant */
+  int32_t thermostat;    /* 1: MBS thermostat after the collision (MPC_SRD only) */
+  int32_t walls_z;       /* 0: periodic in z; 1: no-slip walls at z = 0 and z = Lz */
+  double gravity[3];     /* body-force acceleration g */
+  uint64_t seed;         /* Philox key */
+  uint32_t box_id;       /* Philox counter word 3 (distinguishes boxes with one seed) */
+  uint32_t flags;        /* MPC_FLAG_* */
+  int32_t capacity;      /* particles per brick buffer; 0 = chosen from n_c */
+  int32_t graph_steps;   /* steps per captured CUDA graph; 0 = default (16) */
+} mpc_params;
+
+/* Device-memory provider.  alloc returns device memory of `bytes` (>= 256-byte aligned)
+ * usable on `stream`, or NULL; release returns it.  Passing NULL to mpc_create uses
+ * cudaMalloc/cudaFree. */
+typedef struct {
+  void* ctx;
+  void* (*alloc)(void* ctx, size_t bytes, void* stream);
+  void (*release)(void* ctx, void* ptr, size_t bytes, void* stream);
+} mpc_allocator;
+
+typedef struct {
+  double momentum[3];    /* sum m v after the last step */
+  double ekin;           /* sum m v^2 / 2 */
+  double temperature;    /* m sum |v - <v>|^2 / (3 (N - 1)), k_B = 1 */
+  double stress_kin[3];  /* -(m/V) sum v_a v_b with the streaming velocity: xy, yz, zx */
+  double stress_col[6];  /* -(m/(V h)) sum dv_a rho_b (collisional): xy, yx, yz, zy, zx, xz */
+  int64_t n_particles;
+  int64_t step;          /* number of completed steps */
+  int32_t has_stress;    /* 1 if the stresses were accumulated inside the last step */
+  int32_t reserved;
+} mpc_obs;
+
+typedef struct {
+  int64_t n_particles;
+  int64_t n_cells;       /* Lx Ly (Lz + walls_z): cells of the shifted lattice */
+  int64_t step;          /* completed steps */
+  int32_t fixed_bits;    /* F */
+  int32_t capacity;      /* particles per brick buffer */
+  int32_t brick[3];      /* cells per brick along x, y, z */
+  int32_t n_bricks[3];
+  uint64_t device_bytes; /* device memory held by the handle */
+  int32_t recoveries;    /* capacity overflows repaired so far */
+  int32_t reserved;
+} mpc_info;
+
+/* Create a box, initialise it (Sec. II: uniform positions, Maxwell-Boltzmann velocities
+ * with the net momentum removed, ids 0..N-1) and bin it for step 0.
+ * p: parameters (copied).  stream: cudaStream_t or NULL.  alloc: NULL or a provider
+ * that must outlive the handle.  out: receives the handle.  Synchronises the stream. */
+mpc_status mpc_create(const mpc_params* p, void* stream, const mpc_allocator* alloc,
+                      mpc_handle* out);
+
+/* Release every device buffer of the handle (after finishing its queued work). */
+mpc_status mpc_destroy(mpc_handle h);
+
+/* Enqueue nsteps >= 0 MPC steps (graph-captured in chunks); asynchronous.  A capacity
+ * overflow inside the queued steps stops the chain at a consistent step; the next
+ * synchronising call repairs it and runs the remaining steps. */
+mpc_status mpc_step(mpc_handle h, int64_t nsteps);
+
+/* Wait for queued steps, repair capacity overflows, report device-side errors. */
+mpc_status mpc_synchronize(mpc_handle h);
+
+/* Copy the state out, ordered by unshifted cell index (Sec. III.G.2: checkpoints are
+ * sorted by unshifted cell), arbitrary order inside a cell.
+ * X: 3N uint32, V: 3N float, id: N uint32 or NULL, cell: N uint32 or NULL (collision
+ * cell of each particle in the last step; needs MPC_FLAG_DEBUG_CELLS), step: or NULL.
+ * device_ptrs = 0: host buffers; 1: device buffers.  Synchronises. */
+mpc_status mpc_get_state(mpc_handle h, uint32_t* X, float* V, uint32_t* id, uint32_t* cell,
+                         int64_t* step, int device_ptrs);
+
+/* Replace the state (N particles, same N as the handle) and the step counter.
+ * X values must lie in [0, L << F) (MPC_EINVAL otherwise).  Synchronises. */
+mpc_status mpc_set_state(mpc_handle h, const uint32_t* X, const float* V, const uint32_t* id,
+                         int64_t step, int device_ptrs);
+
+/* Per-cell particle counts of the last step (n_cells uint32; MPC_FLAG_DEBUG_CELLS). */
+mpc_status mpc_get_cell_counts(mpc_handle h, uint32_t* counts, int device_ptrs);
+
+/* Observables after the last completed step (Sec. II: conserved momentum and energy;
+ * stress for Green-Kubo viscosity).  Synchronises. */
+mpc_status mpc_observables(mpc_handle h, mpc_obs* out);
+
+/* Up to `count` most recent per-step rows (oldest first) of the observables ring
+ * (needs MPC_FLAG_OBSERVABLES): row = {px,py,pz, 2 ekin/m, skin xy,yz,zx, scol xy,yx,
+ * yz,zy,zx,xz, step, 0, 0} as raw sums (see mpc_obs for the scalings).  Returns the
+ * number of rows written in *written.  Synchronises. */
+mpc_status mpc_observable_series(mpc_handle h, double* rows, int64_t count, int64_t* written);
+
+mpc_status mpc_get_info(mpc_handle h, mpc_info* out);
+
+/* Text of the last error on h (or of the last failed create when h is NULL). */
+const char* mpc_last_error(mpc_handle h);
+
+/* Library version string. */
+const char* mpc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPC_H */

@@ -86,12 +86,14 @@ def lib():
             L.orc_shift.argtypes = [P(Params), i64, P(u32)]
             L.orc_init.argtypes = [P(Params), i64, P(u32), P(f64), P(u32)]
             L.orc_step.argtypes = [P(Params), i64, P(u32), P(f64), P(u32), i64, P(u32), P(u32),
-                                   P(f64), P(f64), P(ctypes.c_uint8)]
+                                   P(f64), P(f64), P(ctypes.c_uint8), P(f64)]
             L.orc_step.restype = ctypes.c_int
             L.orc_cell_of.argtypes = [P(Params), P(u32), P(u32), P(u32), P(f64)]
             L.orc_srd_axis.argtypes = [P(Params), i64, u32, P(f64)]
             L.orc_rotate.argtypes = [P(f64), f64, P(f64), P(f64)]
             L.orc_stream_one.argtypes = [P(Params), P(u32), P(f64)]
+            L.orc_min_eigenvalue_sym3.argtypes = [P(f64)]
+            L.orc_min_eigenvalue_sym3.restype = f64
             L.orc_sample_normal.argtypes = [ctypes.c_uint64, i64, P(f64)]
             L.orc_sample_gamma.argtypes = [ctypes.c_uint64, f64, i64, P(f64)]
             L.orc_sample_poisson.argtypes = [ctypes.c_uint64, f64, i64, P(ctypes.c_int32)]
@@ -139,7 +141,7 @@ def init(p: Params):
 
 
 def step(p: Params, X, V, ids, step_index: int, cells=False, counts=False, vpre=False,
-         obs=False, flags=False):
+         obs=False, flags=False, sens=False):
     """One MPC step in place on copies of (X, V); returns a dict with the new state and
     the requested diagnostics."""
     X = np.ascontiguousarray(X, dtype=np.uint32).copy()
@@ -153,10 +155,12 @@ def step(p: Params, X, V, ids, step_index: int, cells=False, counts=False, vpre=
     vp = np.zeros((3, N), dtype=np.float64) if vpre else None
     ob = np.zeros(16, dtype=np.float64) if obs else None
     fl = np.zeros(C, dtype=np.uint8) if flags else None
+    se = np.zeros(N, dtype=np.float64) if sens else None
     rc = lib().orc_step(ctypes.byref(p), N, _ptr(X, ctypes.c_uint32), _ptr(V, ctypes.c_double),
                         _ptr(ids, ctypes.c_uint32), step_index, _ptr(cell, ctypes.c_uint32),
                         _ptr(cnt, ctypes.c_uint32), _ptr(vp, ctypes.c_double),
-                        _ptr(ob, ctypes.c_double), _ptr(fl, ctypes.c_uint8))
+                        _ptr(ob, ctypes.c_double), _ptr(fl, ctypes.c_uint8),
+                        _ptr(se, ctypes.c_double))
     if rc != 0:
         raise MemoryError("oracle step failed")
     if cells:
@@ -169,6 +173,11 @@ def step(p: Params, X, V, ids, step_index: int, cells=False, counts=False, vpre=
         out["obs"] = dict(zip(OBS_NAMES, ob[:len(OBS_NAMES)]))
     if flags:
         out["flags"] = fl
+    if sens:
+        # per particle: |r_ic| sum_j |r_jc||w_j| / lambda_min(J) for the angular-momentum
+        # variants (0 for SRD): how strongly float32 rounding of the cell sums is
+        # amplified into this particle's new velocity
+        out["sens"] = se
     return out
 
 
@@ -214,6 +223,11 @@ def stream_one(p: Params, x, v):
     va = np.asarray(v, dtype=np.float64).copy()
     lib().orc_stream_one(ctypes.byref(p), _ptr(xa, ctypes.c_uint32), _ptr(va, ctypes.c_double))
     return xa, va
+
+
+def min_eigenvalue_sym3(A) -> float:
+    a = np.ascontiguousarray(A, dtype=np.float64).reshape(9)
+    return lib().orc_min_eigenvalue_sym3(_ptr(a, ctypes.c_double))
 
 
 def sample_normal(seed: int, n: int) -> np.ndarray:

@@ -314,6 +314,49 @@ static void cross3(const double a[3], const double b[3], double out[3]) {
   out[2] = a[0] * b[1] - a[1] * b[0];
 }
 
+/* smallest eigenvalue of a symmetric 3x3 matrix, closed form of O. K. Smith,
+ * "Eigenvalues of a symmetric 3x3 matrix", CACM 4 (1961) */
+static double min_eigenvalue_sym3(const double A[3][3]) {
+  double p1 = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
+  double q = (A[0][0] + A[1][1] + A[2][2]) / 3.0;
+  if (p1 == 0.0) {
+    double m = A[0][0];
+    if (A[1][1] < m) m = A[1][1];
+    if (A[2][2] < m) m = A[2][2];
+    return m;
+  }
+  double p2 = (A[0][0] - q) * (A[0][0] - q) + (A[1][1] - q) * (A[1][1] - q) +
+              (A[2][2] - q) * (A[2][2] - q) + 2.0 * p1;
+  double pp = sqrt(p2 / 6.0);
+  double B[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) B[a][b] = (A[a][b] - (a == b ? q : 0.0)) / pp;
+  double detB = B[0][0] * (B[1][1] * B[2][2] - B[1][2] * B[2][1]) -
+                B[0][1] * (B[1][0] * B[2][2] - B[1][2] * B[2][0]) +
+                B[0][2] * (B[1][0] * B[2][1] - B[1][1] * B[2][0]);
+  double r = detB / 2.0;
+  if (r < -1.0) r = -1.0;
+  if (r > 1.0) r = 1.0;
+  double phi = acos(r) / 3.0;
+  return q + 2.0 * pp * cos(phi + 2.0 * M_PI / 3.0);
+}
+
+/* rounding-sensitivity of omega x r_ic for a float32 evaluation: |r_i| sum_j |r_j||w_j|
+ * divided by the smallest eigenvalue of J on the space it inverts (test diagnostics) */
+static double omega_sensitivity(int64_t n, const double J[3][3], const double pair_axis[3],
+                                double sum_rw) {
+  if (n <= 1) return 0.0;
+  double lam;
+  if (n == 2) {
+    double d2 = pair_axis[0] * pair_axis[0] + pair_axis[1] * pair_axis[1] +
+                pair_axis[2] * pair_axis[2];
+    lam = 0.5 * d2;
+  } else {
+    lam = min_eigenvalue_sym3(J);
+  }
+  return lam > 0.0 ? sum_rw / lam : INFINITY;
+}
+
 /* omega = J^{-1} Lr for the geometric moment-of-inertia tensor J of a cell
  * (n >= 3: inverse; n == 2: pseudo-inverse on the plane normal to the pair axis;
  * otherwise zero).  Returns flags. */
@@ -383,7 +426,7 @@ int orc_init(const orc_params* p, int64_t N, uint32_t* X, double* V, uint32_t* i
 /* One MPC step (step index `step`) applied to the state (X, V, id) in place. */
 int orc_step(const orc_params* p, int64_t N, uint32_t* X, double* V, const uint32_t* id,
              int64_t step, uint32_t* cell_out, uint32_t* count_out, double* vpre_out,
-             double* obs_out, uint8_t* cell_flags) {
+             double* obs_out, uint8_t* cell_flags, double* sens_out) {
   geom_t g = make_geom(p);
   const int64_t C = orc_num_cells(p);
   const double m = p->m;
@@ -506,6 +549,7 @@ int orc_step(const orc_params* p, int64_t N, uint32_t* X, double* V, const uint3
         for (int a = 0; a < 3; ++a) rel[a] = vb[3 * i + a] - vcm[a];
         orc_rotate(axis, alpha, rel, rot);
         for (int a = 0; a < 3; ++a) vnew[3 * i + a] = vcm[a] + kappa * rot[a];
+        if (sens_out) sens_out[i] = 0.0;
       }
     } else {
       /* angular-momentum-conserving variants: centre-of-mass frame of the cell */
@@ -517,6 +561,7 @@ int orc_step(const orc_params* p, int64_t N, uint32_t* X, double* V, const uint3
       double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
       double Lr[3] = {0, 0, 0};
       double pair_axis[3] = {0, 0, 0};
+      double sum_rw = 0.0;
       if (n == 2)
         for (int a = 0; a < 3; ++a) pair_axis[a] = rho[3 * mem[0] + a] - rho[3 * mem[1] + a];
 
@@ -549,9 +594,11 @@ int orc_step(const orc_params* p, int64_t N, uint32_t* X, double* V, const uint3
             for (int b = 0; b < 3; ++b) J[a][b] += (a == b ? r2 : 0.0) - r[a] * r[b];
           cross3(r, w, rxw);
           for (int a = 0; a < 3; ++a) Lr[a] += rxw[a];
+          sum_rw += sqrt(r2) * sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
         }
         double omega[3];
         flags |= solve_inertia(n, J, Lr, pair_axis, omega);
+        double sens = sens_out ? omega_sensitivity(n, J, pair_axis, sum_rw) : 0.0;
         for (int64_t k = 0; k < n; ++k) {
           int64_t i = mem[k];
           double r[3], wxr[3];
@@ -559,6 +606,7 @@ int orc_step(const orc_params* p, int64_t N, uint32_t* X, double* V, const uint3
           cross3(omega, r, wxr);
           for (int a = 0; a < 3; ++a)
             vnew[3 * i + a] = vcm[a] + vran[3 * k + a] - vrm[a] + wxr[a];
+          if (sens_out) sens_out[i] = sens * sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
         }
         free(vran);
       } else {
@@ -582,15 +630,18 @@ int orc_step(const orc_params* p, int64_t N, uint32_t* X, double* V, const uint3
             for (int b = 0; b < 3; ++b) J[a][b] += (a == b ? r2 : 0.0) - r[a] * r[b];
           cross3(r, w, rxw);
           for (int a = 0; a < 3; ++a) Lr[a] += rxw[a];
+          sum_rw += sqrt(r2) * sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
         }
         double omega[3];
         flags |= solve_inertia(n, J, Lr, pair_axis, omega);
+        double sens = sens_out ? omega_sensitivity(n, J, pair_axis, sum_rw) : 0.0;
         for (int64_t k = 0; k < n; ++k) {
           int64_t i = mem[k];
           double r[3], wxr[3];
           for (int a = 0; a < 3; ++a) r[a] = rho[3 * i + a] - rcm[a];
           cross3(omega, r, wxr);
           for (int a = 0; a < 3; ++a) vnew[3 * i + a] = vcm[a] + dv[3 * k + a] + wxr[a];
+          if (sens_out) sens_out[i] = sens * sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
         }
         free(dv);
       }
@@ -640,6 +691,11 @@ int orc_step(const orc_params* p, int64_t N, uint32_t* X, double* V, const uint3
 
   free(cell); free(rho); free(vb); free(start); free(members); free(fill); free(vnew);
   return 0;
+}
+
+double orc_min_eigenvalue_sym3(const double A[9]) {
+  double M[3][3] = {{A[0], A[1], A[2]}, {A[3], A[4], A[5]}, {A[6], A[7], A[8]}};
+  return min_eigenvalue_sym3(M);
 }
 
 /* ------------------------------------------------------------------------------ */

@@ -65,7 +65,7 @@ int orc_init(const orc_params* p, int64_t N, uint32_t* X, double* V, uint32_t* i
 
 int orc_step(const orc_params* p, int64_t N, uint32_t* X, double* V, const uint32_t* id,
              int64_t step, uint32_t* cell_out, uint32_t* count_out, double* vpre_out,
-             double* obs_out, uint8_t* cell_flags);
+             double* obs_out, uint8_t* cell_flags, double* sens_out);
 
 /* building blocks exposed for the pin tests */
 int orc_cell_of(const orc_params* p, const uint32_t x[3], const uint32_t S[3],
@@ -73,6 +73,7 @@ int orc_cell_of(const orc_params* p, const uint32_t x[3], const uint32_t S[3],
 void orc_srd_axis(const orc_params* p, int64_t step, uint32_t cell, double axis[3]);
 void orc_rotate(const double axis[3], double alpha_rad, const double v[3], double out[3]);
 void orc_stream_one(const orc_params* p, uint32_t x[3], double v[3]);
+double orc_min_eigenvalue_sym3(const double A[9]);
 void orc_sample_normal(uint64_t seed, int64_t n, double* out);
 void orc_sample_gamma(uint64_t seed, double shape, int64_t n, double* out);
 void orc_sample_poisson(uint64_t seed, double lambda, int64_t n, int32_t* out);

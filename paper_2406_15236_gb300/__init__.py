@@ -1,0 +1,303 @@
+"""Python binding of the GB300 MPC step library (C ABI in include/mpc.h).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels of
+``csrc/``.  Functions carry the C names (``mpc_create``, ``mpc_step``, ...); the
+``Simulation`` class wraps a handle.  PyTorch supplies device memory (through the
+handle's allocator callbacks) and the CUDA stream.
+
+The library must be built (``paper_2406_15236_gb300._build.build()``) before import;
+there is no CPU fallback -- import fails loudly when the CUDA library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+_LIB_PATH = _build.LIB
+
+MPC_SRD, MPC_AT_A, MPC_SRD_A = 0, 1, 2
+MPC_OK, MPC_EINVAL, MPC_ENOMEM, MPC_ECUDA, MPC_ETIMEOUT, MPC_ESTATE = range(6)
+MPC_FLAG_OBSERVABLES, MPC_FLAG_DEBUG_CELLS = 1, 2
+STATUS_NAMES = {0: "MPC_OK", 1: "MPC_EINVAL", 2: "MPC_ENOMEM", 3: "MPC_ECUDA",
+                4: "MPC_ETIMEOUT", 5: "MPC_ESTATE"}
+OBS_ROW = ["px", "py", "pz", "sum_v2", "skin_xy", "skin_yz", "skin_zx", "scol_xy", "scol_yx",
+           "scol_yz", "scol_zy", "scol_zx", "scol_xz", "step", "r0", "r1"]
+
+
+class MpcError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class mpc_params(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32 * 3), ("a", ctypes.c_double), ("n_c", ctypes.c_double),
+                ("h", ctypes.c_double), ("alpha_deg", ctypes.c_double), ("kT", ctypes.c_double),
+                ("m", ctypes.c_double), ("variant", ctypes.c_int32),
+                ("thermostat", ctypes.c_int32), ("walls_z", ctypes.c_int32),
+                ("gravity", ctypes.c_double * 3), ("seed", ctypes.c_uint64),
+                ("box_id", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("capacity", ctypes.c_int32), ("graph_steps", ctypes.c_int32)]
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                               ctypes.c_void_p)
+
+
+class mpc_allocator(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("alloc", _ALLOC_FN), ("release", _RELEASE_FN)]
+
+
+class mpc_obs(ctypes.Structure):
+    _fields_ = [("momentum", ctypes.c_double * 3), ("ekin", ctypes.c_double),
+                ("temperature", ctypes.c_double), ("stress_kin", ctypes.c_double * 3),
+                ("stress_col", ctypes.c_double * 6), ("n_particles", ctypes.c_int64),
+                ("step", ctypes.c_int64), ("has_stress", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class mpc_info(ctypes.Structure):
+    _fields_ = [("n_particles", ctypes.c_int64), ("n_cells", ctypes.c_int64),
+                ("step", ctypes.c_int64), ("fixed_bits", ctypes.c_int32),
+                ("capacity", ctypes.c_int32), ("brick", ctypes.c_int32 * 3),
+                ("n_bricks", ctypes.c_int32 * 3), ("device_bytes", ctypes.c_uint64),
+                ("recoveries", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """Load the CUDA library; raises if it was not built (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"CUDA library {_LIB_PATH} is missing: run "
+                          "paper_2406_15236_gb300._build.build() (needs nvcc, sm_103a)")
+    L = ctypes.CDLL(_LIB_PATH)
+    P, vp = ctypes.POINTER, ctypes.c_void_p
+    L.mpc_create.argtypes = [P(mpc_params), vp, P(mpc_allocator), P(vp)]
+    L.mpc_destroy.argtypes = [vp]
+    L.mpc_step.argtypes = [vp, ctypes.c_int64]
+    L.mpc_synchronize.argtypes = [vp]
+    L.mpc_get_state.argtypes = [vp, vp, vp, vp, vp, P(ctypes.c_int64), ctypes.c_int]
+    L.mpc_set_state.argtypes = [vp, vp, vp, vp, ctypes.c_int64, ctypes.c_int]
+    L.mpc_get_cell_counts.argtypes = [vp, vp, ctypes.c_int]
+    L.mpc_observables.argtypes = [vp, P(mpc_obs)]
+    L.mpc_observable_series.argtypes = [vp, vp, ctypes.c_int64, P(ctypes.c_int64)]
+    L.mpc_get_info.argtypes = [vp, P(mpc_info)]
+    L.mpc_last_error.argtypes = [vp]
+    L.mpc_last_error.restype = ctypes.c_char_p
+    L.mpc_version.restype = ctypes.c_char_p
+    for name in ("mpc_create", "mpc_destroy", "mpc_step", "mpc_synchronize", "mpc_get_state",
+                 "mpc_set_state", "mpc_get_cell_counts", "mpc_observables",
+                 "mpc_observable_series", "mpc_get_info"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(status, handle=None):
+    if status != MPC_OK:
+        msg = lib().mpc_last_error(handle)
+        raise MpcError(status, msg.decode() if msg else "")
+
+
+def make_params(L=(16, 16, 16), n_c=10.0, h=0.1, alpha_deg=130.0, kT=1.0, m=1.0,
+                variant=MPC_SRD, thermostat=0, walls_z=0, gravity=(0.0, 0.0, 0.0), seed=1,
+                box_id=0, flags=0, capacity=0, graph_steps=0) -> mpc_params:
+    if isinstance(L, int):
+        L = (L, L, L)
+    p = mpc_params()
+    p.L[:] = list(L)
+    p.a = 1.0
+    p.n_c, p.h, p.alpha_deg, p.kT, p.m = n_c, h, alpha_deg, kT, m
+    p.variant, p.thermostat, p.walls_z = variant, thermostat, walls_z
+    p.gravity[:] = list(gravity)
+    p.seed, p.box_id, p.flags = seed, box_id, flags
+    p.capacity, p.graph_steps = capacity, graph_steps
+    return p
+
+
+def torch_allocator():
+    """An mpc_allocator backed by PyTorch's caching allocator on the current device."""
+    import torch
+
+    device = torch.cuda.current_device()
+
+    @_ALLOC_FN
+    def _alloc(ctx, nbytes, stream):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device, int(stream or 0))
+        except Exception:  # out of memory -> NULL, reported as MPC_ENOMEM
+            return None
+
+    @_RELEASE_FN
+    def _release(ctx, ptr, nbytes, stream):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a = mpc_allocator()
+    a.ctx = None
+    a.alloc = _alloc
+    a.release = _release
+    return a
+
+
+# --- C-ABI functions, same names -------------------------------------------------------
+
+def mpc_version() -> str:
+    return lib().mpc_version().decode()
+
+
+def mpc_last_error(handle=None) -> str:
+    s = lib().mpc_last_error(handle)
+    return s.decode() if s else ""
+
+
+def mpc_create(params: mpc_params, stream=None, allocator: mpc_allocator | None = None):
+    h = ctypes.c_void_p()
+    st = lib().mpc_create(ctypes.byref(params), ctypes.c_void_p(stream or 0),
+                          ctypes.byref(allocator) if allocator is not None else None,
+                          ctypes.byref(h))
+    _check(st)
+    return h
+
+
+def mpc_destroy(handle) -> None:
+    _check(lib().mpc_destroy(handle), handle)
+
+
+def mpc_step(handle, nsteps: int) -> None:
+    _check(lib().mpc_step(handle, int(nsteps)), handle)
+
+
+def mpc_synchronize(handle) -> None:
+    _check(lib().mpc_synchronize(handle), handle)
+
+
+def _addr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()  # torch tensor
+
+
+def mpc_get_state(handle, X, V, ids=None, cell=None, device_ptrs=False) -> int:
+    step = ctypes.c_int64()
+    _check(lib().mpc_get_state(handle, _addr(X), _addr(V), _addr(ids), _addr(cell),
+                               ctypes.byref(step), int(bool(device_ptrs))), handle)
+    return step.value
+
+
+def mpc_set_state(handle, X, V, ids, step: int, device_ptrs=False) -> None:
+    _check(lib().mpc_set_state(handle, _addr(X), _addr(V), _addr(ids), int(step),
+                               int(bool(device_ptrs))), handle)
+
+
+def mpc_get_cell_counts(handle, counts, device_ptrs=False) -> None:
+    _check(lib().mpc_get_cell_counts(handle, _addr(counts), int(bool(device_ptrs))), handle)
+
+
+def mpc_observables(handle) -> mpc_obs:
+    o = mpc_obs()
+    _check(lib().mpc_observables(handle, ctypes.byref(o)), handle)
+    return o
+
+
+def mpc_observable_series(handle, rows: np.ndarray) -> int:
+    n = ctypes.c_int64()
+    _check(lib().mpc_observable_series(handle, rows.ctypes.data, rows.shape[0], ctypes.byref(n)),
+           handle)
+    return n.value
+
+
+def mpc_get_info(handle) -> mpc_info:
+    i = mpc_info()
+    _check(lib().mpc_get_info(handle, ctypes.byref(i)), handle)
+    return i
+
+
+# --- convenience wrapper -----------------------------------------------------------------
+
+class Simulation:
+    """One MPC box on the current CUDA device."""
+
+    def __init__(self, stream=None, use_torch_allocator=True, **kw):
+        import torch
+
+        self.params = make_params(**kw)
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        self._alloc = torch_allocator() if use_torch_allocator else None
+        self.handle = mpc_create(self.params, stream, self._alloc)
+        self.info = mpc_get_info(self.handle)
+        self.N = self.info.n_particles
+
+    def step(self, n: int = 1):
+        mpc_step(self.handle, n)
+
+    def synchronize(self):
+        mpc_synchronize(self.handle)
+
+    def get_state(self, cells=False):
+        """(X (3,N) uint32, V (3,N) float32, ids (N,), step[, cell]) on the host, sorted by
+        unshifted cell."""
+        N = self.N
+        X = np.empty((3, N), dtype=np.uint32)
+        V = np.empty((3, N), dtype=np.float32)
+        ids = np.empty(N, dtype=np.uint32)
+        cell = np.empty(N, dtype=np.uint32) if cells else None
+        step = mpc_get_state(self.handle, X, V, ids, cell)
+        return (X, V, ids, step, cell) if cells else (X, V, ids, step)
+
+    def set_state(self, X, V, ids, step):
+        X = np.ascontiguousarray(X, dtype=np.uint32)
+        V = np.ascontiguousarray(V, dtype=np.float32)
+        ids = np.ascontiguousarray(ids, dtype=np.uint32)
+        mpc_set_state(self.handle, X, V, ids, step)
+
+    def cell_counts(self):
+        c = np.empty(self.info.n_cells, dtype=np.uint32)
+        mpc_get_cell_counts(self.handle, c)
+        return c
+
+    def observables(self) -> dict:
+        o = mpc_observables(self.handle)
+        return {"momentum": np.array(o.momentum[:]), "ekin": o.ekin,
+                "temperature": o.temperature, "stress_kin": np.array(o.stress_kin[:]),
+                "stress_col": np.array(o.stress_col[:]), "n_particles": o.n_particles,
+                "step": o.step, "has_stress": bool(o.has_stress)}
+
+    def observable_series(self, count: int) -> np.ndarray:
+        rows = np.zeros((count, 16), dtype=np.float64)
+        n = mpc_observable_series(self.handle, rows)
+        return rows[:n]
+
+    def close(self):
+        if self.handle is not None:
+            mpc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,174 @@
+// Device building blocks of the MPC step: counter-based random numbers, samplers,
+// the fixed-point streaming contract and the shifted-lattice cell assignment.
+//
+// Everything here follows the written state contract of include/mpc.h; the float32
+// expressions whose result decides an integer (the gamma sampler's accept/reject, the
+// displacement rounding) use explicitly rounded intrinsics so the compiler cannot
+// contract them into FMAs.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mpc_internal.h"
+
+namespace mpc {
+
+// Philox counter word 2 = (tag << 24) | sub-draw index.  Tag values are part of the
+// keying contract.
+enum : uint32_t {
+  kTagShift = 1, kTagAxis = 2, kTagMbs = 3, kTagPhantom = 4, kTagPhGamma = 5,
+  kTagAtVel = 6, kTagInitX = 7, kTagInitV = 8
+};
+
+// Philox4x32-10 (Salmon et al., SC'11): per round, the two multiplier words give
+// 64-bit products whose high halves are mixed into the other pair of words with the
+// round key; the key advances by the Weyl increments after every round.
+__device__ __forceinline__ uint4 philox4x32(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                            uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo_a = 0xD2511F53u * c0;
+    const uint32_t hi_a = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo_b = 0xCD9E8D57u * c2;
+    const uint32_t hi_b = __umulhi(0xCD9E8D57u, c2);
+    c0 = hi_b ^ c1 ^ k0;
+    c1 = lo_b;
+    c2 = hi_a ^ c3 ^ k1;
+    c3 = lo_a;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+__device__ __forceinline__ uint4 draw(const Geom& g, uint32_t index, uint32_t step, uint32_t tag,
+                                      uint32_t sub) {
+  return philox4x32(index, step, (tag << 24) | sub, g.box, g.key0, g.key1);
+}
+
+// (k + 1/2) 2^-23 from the top 23 bits: exact in float32
+__device__ __forceinline__ float u01(uint32_t r) {
+  return __fmul_rn(__fadd_rn((float)(r >> 9), 0.5f), 1.1920928955078125e-7f);
+}
+
+// Box-Muller pair of standard normals
+__device__ __forceinline__ float2 normal2(uint32_t ra, uint32_t rb) {
+  const float R = sqrtf(-2.0f * logf(u01(ra)));
+  float s, c;
+  sincospif(2.0f * u01(rb), &s, &c);
+  return make_float2(R * c, R * s);
+}
+
+// Gamma(shape a >= 1, scale 1), Marsaglia & Tsang (ACM TOMS 26, 2000); attempt k uses
+// Philox(index, step, tag, k).  Float32 decisions in a fixed evaluation order.
+__device__ __forceinline__ float gamma_mt(const Geom& g, uint32_t index, uint32_t step, uint32_t tag,
+                                          float a) {
+  const float d = __fsub_rn(a, 1.0f / 3.0f);
+  const float c = __fdiv_rn(1.0f, __fsqrt_rn(__fmul_rn(9.0f, d)));
+  for (uint32_t k = 0; k < 32; ++k) {
+    const uint4 r = draw(g, index, step, tag, k);
+    const float x = normal2(r.x, r.y).x;
+    const float u = u01(r.z);
+    const float v1 = __fmaf_rn(c, x, 1.0f);
+    if (v1 <= 0.0f) continue;
+    const float v3 = __fmul_rn(__fmul_rn(v1, v1), v1);
+    const float x2 = __fmul_rn(x, x);
+    const float x4 = __fmul_rn(x2, x2);
+    const float squeeze = __fsub_rn(1.0f, __fmul_rn(0.0331f, x4));
+    if (u < squeeze) return d * v3;
+    const float rhs =
+        __fadd_rn(__fmul_rn(0.5f, x2), __fmul_rn(d, __fadd_rn(__fsub_rn(1.0f, v3), logf(v3))));
+    if (logf(u) < rhs) return d * v3;
+  }
+  return d;
+}
+
+// Poisson(lambda) by sequential CDF inversion in float64 (wall cells only)
+__device__ __forceinline__ int poisson_inv(double u, double lambda) {
+  int k = 0;
+  double prob = exp(-lambda);
+  double cdf = prob;
+  while (u > cdf && k < 100000) {
+    ++k;
+    prob *= lambda / (double)k;
+    cdf += prob;
+  }
+  return k;
+}
+
+__device__ __forceinline__ uint3 lattice_shift(const Geom& g, uint32_t step) {
+  const uint4 r = draw(g, 0u, step, kTagShift, 0u);
+  const int sh = 32 - g.F;
+  return make_uint3(r.x >> sh, r.y >> sh, r.z >> sh);
+}
+
+// float32 product v * (h 2^F) rounded half-to-even, saturated (NaN -> 0), clamped
+__device__ __forceinline__ int displacement(float v, float hs, uint32_t P) {
+  int d = __float2int_rn(__fmul_rn(v, hs));
+  const int lim = (int)(P - 1u);
+  return max(-lim, min(lim, d));
+}
+
+__device__ __forceinline__ uint32_t wrap(int64_t t, uint32_t P) {
+  if (t < 0) t += (int64_t)P;
+  else if (t >= (int64_t)P) t -= (int64_t)P;
+  return (uint32_t)t;
+}
+
+// round(num / den) to nearest, ties to even, exact integers (den != 0)
+__device__ __forceinline__ int64_t rdiv_half_even(int64_t num, int64_t den) {
+  if (den < 0) { num = -num; den = -den; }
+  int64_t q = num / den;
+  int64_t r = num - q * den;  // sign of num
+  const int64_t twice = 2 * (r < 0 ? -r : r);
+  if (twice > den || (twice == den && (q & 1))) q += (num < 0) ? -1 : 1;
+  return q;
+}
+
+// Eq. (1) with gravity kick and boundary conditions.  (x, v) in; x out is the streamed
+// position, v out the velocity entering the collision (reversed after a wall hit).
+__device__ __forceinline__ void stream(const Geom& g, uint32_t& x, uint32_t& y, uint32_t& z,
+                                       float& vx, float& vy, float& vz) {
+  vx = __fadd_rn(vx, g.gh[0]);
+  vy = __fadd_rn(vy, g.gh[1]);
+  vz = __fadd_rn(vz, g.gh[2]);
+  int dx = displacement(vx, g.hs, g.P[0]);
+  int dy = displacement(vy, g.hs, g.P[1]);
+  const int dz = displacement(vz, g.hs, g.P[2]);
+  if (g.walls) {
+    const int64_t Z = z;
+    const int64_t zn = Z + dz;
+    const int64_t Pz = g.P[2];
+    if (zn >= Pz || zn < 0) {
+      const int64_t Znew = (zn >= Pz) ? (2 * Pz - 1 - zn) : (-1 - zn);
+      dx = (int)rdiv_half_even((int64_t)dx * (Znew - Z), (int64_t)dz);
+      dy = (int)rdiv_half_even((int64_t)dy * (Znew - Z), (int64_t)dz);
+      z = (uint32_t)Znew;
+      vx = -vx;
+      vy = -vy;
+      vz = -vz;
+    } else {
+      z = (uint32_t)zn;
+    }
+  } else {
+    z = wrap((int64_t)z + dz, g.P[2]);
+  }
+  x = wrap((int64_t)x + dx, g.P[0]);
+  y = wrap((int64_t)y + dy, g.P[1]);
+}
+
+// cell of the shifted lattice, per axis; periodic axes wrap index L to 0
+__device__ __forceinline__ int cell_axis(const Geom& g, uint32_t x, uint32_t s, int ax) {
+  int c = (int)((x + s) >> g.F);
+  if (c >= g.L[ax] && (ax < 2 || !g.walls)) c -= g.L[ax];
+  return c;
+}
+
+// position relative to the cell centre, in units of a
+__device__ __forceinline__ float rho_axis(const Geom& g, uint32_t x, uint32_t s) {
+  const int u = (int)((x + s) & g.mask) - (int)(1u << (g.F - 1));
+  return __fmul_rn((float)u, g.inv2F);
+}
+
+}  // namespace mpc

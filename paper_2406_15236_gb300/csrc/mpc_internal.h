@@ -1,0 +1,116 @@
+// Internal types shared by the host API and the kernels of the MPC library.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mpc {
+
+// Everything a kernel needs to know about one box (passed by value).
+struct Geom {
+  int L[3];          // box edge in cells
+  int Lc[3];         // extent of the collision-cell grid (Lz + 1 layers with walls)
+  uint32_t P[3];     // L << F
+  int F;             // fixed-point fraction bits
+  uint32_t mask;     // 2^F - 1
+  float hs;          // float32(h 2^F)
+  float gh[3];       // float32(g h)
+  float inv2F;       // 2^-F
+  int walls;         // no-slip walls at z = 0, Lz
+  int B[3];          // cells per brick
+  int nb[3];         // bricks per axis
+  int nbricks;
+  int cap;           // particles per brick buffer
+  int brick_cells;   // B[0] B[1] B[2]
+  int variant;       // 0 SRD, 1 AT+a, 2 SRD+a
+  int thermostat;    // MBS after SRD
+  float cos_a, sin_a;
+  float sigma;       // sqrt(kT / m)
+  float kT, m;
+  double n_c;        // mean density (phantom particles)
+  uint32_t key0, key1, box;
+  int obs;           // accumulate observables
+  int debug;         // keep collision cells and per-cell counts
+  int64_t ncells;    // Lc[0] Lc[1] Lc[2]
+};
+
+// Device-side control block of a box; written by the step kernels.
+struct Ctrl {
+  int64_t step;           // completed steps
+  int32_t halted;         // a brick overflowed: later steps are skipped until repaired
+  int32_t overflow;       // set during the step that overflowed
+  int32_t lost;           // the spill area overflowed as well (state unrecoverable)
+  int32_t errors;         // bit flags, see kErr*
+  uint32_t spill_count;
+  uint32_t pad;
+};
+
+enum : int32_t { kErrBinning = 1, kErrTimeout = 2, kErrRange = 4 };
+
+// Particle buffer set: structure of arrays, nbricks * cap entries each.
+struct PBuf {
+  uint32_t* x[3];
+  float* v[3];
+  uint32_t* id;
+  uint32_t* cell;  // collision cell of the last step (debug only, else nullptr)
+};
+
+struct Spill {
+  uint32_t* x[3];
+  float* v[3];
+  uint32_t* id;
+  uint32_t* cell;
+  uint32_t* dest;
+  uint32_t capacity;
+};
+
+constexpr int kObsSlots = 128;   // partial-sum slots per step (spreads FP64 atomics)
+constexpr int kObsWidth = 16;    // doubles per observables row
+
+struct StepArgs {
+  Geom g;
+  PBuf buf[2];
+  uint32_t* cnt[2];
+  Ctrl* ctrl;
+  Spill spill;
+  double* obs_partials;   // kObsSlots * kObsWidth
+  double* obs_series;     // ring * kObsWidth
+  int obs_ring;
+  uint32_t* dbg_counts;   // ncells (debug)
+};
+
+// launchers (mpc_step.cu)
+size_t step_smem_bytes(const Geom& g);
+cudaError_t configure_step_kernels(const Geom& g);
+cudaError_t launch_step(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_advance(const StepArgs& a, cudaStream_t s);
+
+// launchers (mpc_layout.cu)
+cudaError_t launch_init_particles(const Geom& g, int64_t N, uint32_t* const x[3], float* const v[3],
+                                  uint32_t* id, double* sums, cudaStream_t s);
+cudaError_t launch_sub_mean(int64_t N, float* const v[3], const double* sums, cudaStream_t s);
+cudaError_t launch_bin_count(const Geom& g, int64_t N, uint32_t* const x[3], float* const v[3],
+                             int64_t step, uint32_t* counts, int32_t* errors, cudaStream_t s);
+cudaError_t launch_bin_scatter(const Geom& g, int64_t N, uint32_t* const x[3], float* const v[3],
+                               const uint32_t* id, const uint32_t* cell, int64_t step,
+                               const PBuf& dst, uint32_t* cnt, int32_t* errors, cudaStream_t s);
+cudaError_t launch_check_range(const Geom& g, int64_t N, uint32_t* const x[3], int32_t* errors,
+                               cudaStream_t s);
+cudaError_t launch_max_u32(const uint32_t* in, int64_t n, uint32_t* out, cudaStream_t s);
+// exclusive scan of n uint32 into out (may alias in); tmp must hold scan_tmp_words(n)
+size_t scan_tmp_words(int64_t n);
+cudaError_t launch_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp,
+                        cudaStream_t s);
+cudaError_t launch_compact(const Geom& g, const PBuf& src, const uint32_t* cnt,
+                           const uint32_t* offsets, const PBuf& dst, cudaStream_t s);
+cudaError_t launch_append_spill(const Spill& sp, uint32_t count, uint64_t base, const PBuf& dst,
+                                cudaStream_t s);
+cudaError_t launch_cell_hist(const Geom& g, int64_t N, uint32_t* const x[3], uint32_t* hist,
+                             cudaStream_t s);
+cudaError_t launch_cell_scatter(const Geom& g, int64_t N, const PBuf& src, uint32_t* cursor,
+                                const PBuf& dst, cudaStream_t s);
+cudaError_t launch_reduce_obs(const Geom& g, const PBuf& b, const uint32_t* cnt, double* out,
+                              cudaStream_t s);
+
+}  // namespace mpc

@@ -1,0 +1,604 @@
+// The fused MPC step: one CTA per brick of collision cells.
+//
+// Particles live in fixed-capacity brick buffers, binned by the collision cell they
+// will occupy in the coming step.  For step n a CTA
+//   1. pulls its brick's particles (x, y, z, vx, vy, vz, id: 28 B each) into shared
+//      memory with bulk-async (TMA) copies,
+//   2. streams them (Eq. 1, gravity kick, periodic / bounce-back walls), finds their
+//      cell on the lattice shifted by S(n) (all cells are inside this brick by
+//      construction) and accumulates the per-cell sums with shared-memory atomics,
+//   3. finalises every cell (SRD axis and MBS factor, Eqs. 2 and 5-7, phantom
+//      particles in wall cells; or the AT+a angular velocity),
+//   4. applies the collision to every particle, predicts the cell of step n+1 from the
+//      streamed position and the new velocity, counting-sorts its particles by
+//      destination brick in shared memory, reserves space in each destination with one
+//      global atomic per (CTA, destination), and writes the particles out coalesced.
+// HBM traffic per particle-step is one read and one write of the 28-byte particle:
+// no global per-cell arrays, no second sweep, no separate reorder pass (the permanent
+// reorder of Sec. III.B.3 happens in every step as part of the write).
+#include <cstdio>
+
+#include "mpc_device.cuh"
+#include "mpc_internal.h"
+
+namespace mpc {
+
+constexpr int kThreads = 256;
+
+template <int VAR>
+struct CellSums;
+template <>
+struct CellSums<0> {
+  // SRD: sum v (3); with the thermostat a second pass adds sum |v - v_cm|^2
+  static constexpr int kSums = 4;
+  // v_cm (3), axis (3), kappa, phantom relative kinetic energy, total count
+  static constexpr int kParams = 9;
+};
+template <>
+struct CellSums<1> {
+  // AT+a, two passes: sum rho (3), sum w = v - v_ran (3); then, about the cell's centre
+  // of mass, the second moments M = sum r r^T (6) and L = sum r x (w - <w>) (3)
+  static constexpr int kSums = 15;
+  static constexpr int kParams = 9;  // <w> = v_cm - <v_ran> (3), omega (3), rho_cm (3)
+};
+
+struct Layout {
+  size_t x, y, z, vx, vy, vz, id, gcell, lcell, aux, perm, count, sums, params, total;
+};
+
+__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
+
+__host__ __device__ inline Layout make_layout(int cap, int bc, int nsums, int nparams, int debug) {
+  Layout L;
+  size_t o = 0;
+  const size_t a4 = align16(size_t(cap) * 4);
+  L.x = o; o += a4;
+  L.y = o; o += a4;
+  L.z = o; o += a4;
+  L.vx = o; o += a4;
+  L.vy = o; o += a4;
+  L.vz = o; o += a4;
+  L.id = o; o += a4;
+  L.gcell = o; o += debug ? a4 : 0;
+  L.lcell = o; o += align16(size_t(cap) * 2);
+  L.aux = o; o += a4;
+  L.perm = o; o += align16(size_t(cap) * 2);
+  L.count = o; o += align16(size_t(bc) * 4);
+  L.sums = o; o += align16(size_t(bc) * 4 * nsums);
+  L.params = o; o += align16(size_t(bc) * 4 * nparams);
+  L.total = o;
+  return L;
+}
+
+template <int VAR>
+__host__ __device__ inline Layout layout_for(const Geom& g) {
+  return make_layout(g.cap, g.brick_cells, CellSums<VAR>::kSums, CellSums<VAR>::kParams, g.debug);
+}
+
+// --- small PTX wrappers -----------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// bounded wait on phase `parity`; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t addr = smem_u32(bar);
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// --- the step kernel ---------------------------------------------------------------
+template <int VAR>
+__global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const Geom& g = a.g;
+  constexpr int NS = CellSums<VAR>::kSums;
+  const Layout lay = layout_for<VAR>(g);
+
+  uint32_t* sx = reinterpret_cast<uint32_t*>(smem + lay.x);
+  uint32_t* sy = reinterpret_cast<uint32_t*>(smem + lay.y);
+  uint32_t* sz = reinterpret_cast<uint32_t*>(smem + lay.z);
+  float* svx = reinterpret_cast<float*>(smem + lay.vx);
+  float* svy = reinterpret_cast<float*>(smem + lay.vy);
+  float* svz = reinterpret_cast<float*>(smem + lay.vz);
+  uint32_t* sid = reinterpret_cast<uint32_t*>(smem + lay.id);
+  uint32_t* sgc = reinterpret_cast<uint32_t*>(smem + lay.gcell);
+  uint16_t* slc = reinterpret_cast<uint16_t*>(smem + lay.lcell);
+  uint32_t* saux = reinterpret_cast<uint32_t*>(smem + lay.aux);
+  uint16_t* sperm = reinterpret_cast<uint16_t*>(smem + lay.perm);
+  uint32_t* scount = reinterpret_cast<uint32_t*>(smem + lay.count);
+  float* ssum = reinterpret_cast<float*>(smem + lay.sums);
+  float* spar = reinterpret_cast<float*>(smem + lay.params);
+
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t s_cnt, s_halt;
+  __shared__ uint32_t gcount[28], gstart[29], gbase[28], gdest[28];
+  __shared__ uint32_t sh0[3], sh1[3];
+  __shared__ float s_obs[kThreads / 32][13];
+
+  const int tid = threadIdx.x;
+  const int b = blockIdx.x;
+  const int bc = g.brick_cells;
+
+  if (tid == 0) {
+    s_halt = *(volatile int32_t*)&a.ctrl->halted;
+  }
+  __syncthreads();
+  if (s_halt) return;
+  const int64_t step64 = *(volatile int64_t*)&a.ctrl->step;
+  const uint32_t step = (uint32_t)step64;
+  const int par = (int)(step64 & 1);
+  const PBuf& src = a.buf[par];
+  const PBuf& dst = a.buf[par ^ 1];
+  uint32_t* cnt_src = a.cnt[par];
+  uint32_t* cnt_dst = a.cnt[par ^ 1];
+
+  // ---- 1. load the brick ----
+  if (tid == 0) {
+    uint32_t c = cnt_src[b];
+    if (c > (uint32_t)g.cap) c = g.cap;
+    s_cnt = c;
+    cnt_src[b] = 0;  // this buffer becomes the destination of the next step
+    mbar_init(&bar, 1);
+  }
+  if (tid < 28) gcount[tid] = 0;
+  if (tid == 32) {
+    const uint3 s0 = lattice_shift(g, step);
+    const uint3 s1 = lattice_shift(g, step + 1);
+    sh0[0] = s0.x; sh0[1] = s0.y; sh0[2] = s0.z;
+    sh1[0] = s1.x; sh1[1] = s1.y; sh1[2] = s1.z;
+  }
+  for (int c = tid; c < bc; c += kThreads) {
+    scount[c] = 0;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) ssum[k * bc + c] = 0.0f;
+  }
+  __syncthreads();
+  const int cnt = (int)s_cnt;
+  if (tid == 0) {
+    const uint32_t bytes = (uint32_t)(((cnt + 3) & ~3) * 4);
+    mbar_expect_tx(&bar, 7u * bytes);
+    if (bytes) {
+      const size_t off = (size_t)b * g.cap;
+      bulk_g2s(sx, src.x[0] + off, bytes, &bar);
+      bulk_g2s(sy, src.x[1] + off, bytes, &bar);
+      bulk_g2s(sz, src.x[2] + off, bytes, &bar);
+      bulk_g2s(svx, src.v[0] + off, bytes, &bar);
+      bulk_g2s(svy, src.v[1] + off, bytes, &bar);
+      bulk_g2s(svz, src.v[2] + off, bytes, &bar);
+      bulk_g2s(sid, src.id + off, bytes, &bar);
+    }
+  }
+  if (!mbar_wait(&bar, 0)) {
+    if (tid == 0) atomicOr(&a.ctrl->errors, kErrTimeout);
+    mbar_wait(&bar, 0);  // give copies in flight one more bounded chance before leaving
+    return;
+  }
+
+  const int bx = b % g.nb[0];
+  const int by = (b / g.nb[0]) % g.nb[1];
+  const int bz = b / (g.nb[0] * g.nb[1]);
+  const int ox = bx * g.B[0], oy = by * g.B[1], oz = bz * g.B[2];
+  const uint32_t S0x = sh0[0], S0y = sh0[1], S0z = sh0[2];
+
+  // ---- 2. stream, bin into the cells of this brick, accumulate cell sums ----
+  for (int i = tid; i < cnt; i += kThreads) {
+    uint32_t x = sx[i], y = sy[i], z = sz[i];
+    float vx = svx[i], vy = svy[i], vz = svz[i];
+    stream(g, x, y, z, vx, vy, vz);
+    const int cx = cell_axis(g, x, S0x, 0), cy = cell_axis(g, y, S0y, 1),
+              cz = cell_axis(g, z, S0z, 2);
+    const int lx = cx - ox, ly = cy - oy, lz = cz - oz;
+    int lc;
+    if ((unsigned)lx < (unsigned)g.B[0] && (unsigned)ly < (unsigned)g.B[1] &&
+        (unsigned)lz < (unsigned)g.B[2]) {
+      lc = lx + g.B[0] * (ly + g.B[1] * lz);
+    } else {
+      lc = 0xFFFF;  // not binned here: keep the particle, skip its collision
+      atomicOr(&a.ctrl->errors, kErrBinning);
+    }
+    sx[i] = x; sy[i] = y; sz[i] = z;
+    svx[i] = vx; svy[i] = vy; svz[i] = vz;
+    slc[i] = (uint16_t)lc;
+    if (g.debug) sgc[i] = (uint32_t)cx + (uint32_t)g.Lc[0] * ((uint32_t)cy + (uint32_t)g.Lc[1] * (uint32_t)cz);
+    if (lc == 0xFFFF) continue;
+    atomicAdd(&scount[lc], 1u);
+    if constexpr (VAR == 0) {
+      atomicAdd(&ssum[0 * bc + lc], vx);
+      atomicAdd(&ssum[1 * bc + lc], vy);
+      atomicAdd(&ssum[2 * bc + lc], vz);
+    } else {
+      // AT+a: w = v - v_ran replaces the velocity in shared memory (v_ran is redrawn
+      // from its Philox key when the collision is applied)
+      const uint4 r = draw(g, sid[i], step, kTagAtVel, 0u);
+      const float2 n01 = normal2(r.x, r.y);
+      const float n2 = normal2(r.z, r.w).x;
+      const float wx = vx - g.sigma * n01.x, wy = vy - g.sigma * n01.y, wz = vz - g.sigma * n2;
+      svx[i] = wx; svy[i] = wy; svz[i] = wz;
+      atomicAdd(&ssum[0 * bc + lc], rho_axis(g, x, S0x));
+      atomicAdd(&ssum[1 * bc + lc], rho_axis(g, y, S0y));
+      atomicAdd(&ssum[2 * bc + lc], rho_axis(g, z, S0z));
+      atomicAdd(&ssum[3 * bc + lc], wx);
+      atomicAdd(&ssum[4 * bc + lc], wy);
+      atomicAdd(&ssum[5 * bc + lc], wz);
+    }
+  }
+  __syncthreads();
+
+  if constexpr (VAR == 1) {
+    // second pass: moments about each cell's centre of mass (no cancellation between
+    // a sum of squares and the squared mean, which small cells would suffer)
+    for (int i = tid; i < cnt; i += kThreads) {
+      const int lc = slc[i];
+      if (lc == 0xFFFF) continue;
+      const float inv = 1.0f / (float)scount[lc];
+      const float rx = rho_axis(g, sx[i], S0x) - ssum[0 * bc + lc] * inv;
+      const float ry = rho_axis(g, sy[i], S0y) - ssum[1 * bc + lc] * inv;
+      const float rz = rho_axis(g, sz[i], S0z) - ssum[2 * bc + lc] * inv;
+      const float wx = svx[i] - ssum[3 * bc + lc] * inv;
+      const float wy = svy[i] - ssum[4 * bc + lc] * inv;
+      const float wz = svz[i] - ssum[5 * bc + lc] * inv;
+      atomicAdd(&ssum[6 * bc + lc], rx * rx);
+      atomicAdd(&ssum[7 * bc + lc], ry * ry);
+      atomicAdd(&ssum[8 * bc + lc], rz * rz);
+      atomicAdd(&ssum[9 * bc + lc], rx * ry);
+      atomicAdd(&ssum[10 * bc + lc], ry * rz);
+      atomicAdd(&ssum[11 * bc + lc], rz * rx);
+      atomicAdd(&ssum[12 * bc + lc], ry * wz - rz * wy);
+      atomicAdd(&ssum[13 * bc + lc], rz * wx - rx * wz);
+      atomicAdd(&ssum[14 * bc + lc], rx * wy - ry * wx);
+    }
+    __syncthreads();
+  }
+
+  // ---- 3. finalise every cell of the brick ----
+  for (int lc = tid; lc < bc; lc += kThreads) {
+    const int lx = lc % g.B[0], ly = (lc / g.B[0]) % g.B[1], lz = lc / (g.B[0] * g.B[1]);
+    const int cx = ox + lx, cy = oy + ly, cz = oz + lz;
+    if (cx >= g.Lc[0] || cy >= g.Lc[1] || cz >= g.Lc[2]) continue;
+    const uint32_t cg = (uint32_t)cx + (uint32_t)g.Lc[0] * ((uint32_t)cy + (uint32_t)g.Lc[1] * (uint32_t)cz);
+    const uint32_t n = scount[lc];
+    if (g.debug) a.dbg_counts[cg] = n;
+    if (n == 0) continue;
+    if constexpr (VAR == 0) {
+      const float sumx = ssum[0 * bc + lc], sumy = ssum[1 * bc + lc], sumz = ssum[2 * bc + lc];
+      float nph = 0.0f, Px = 0.0f, Py = 0.0f, Pz = 0.0f, Kint = 0.0f;
+      if (g.walls && (cz == 0 || cz == g.L[2])) {
+        // phantom particles fill the wall part of a cut cell at the mean density
+        // (Sec. II, Boundary conditions): Poisson count, Gaussian momenta, and the
+        // internal kinetic energy of the phantom set ~ kT chi^2(3(n_ph - 1))
+        const double s = (double)sh0[2] * (double)g.inv2F;
+        const double phi = (cz == 0) ? s : 1.0 - s;
+        const uint4 r = draw(g, cg, step, kTagPhantom, 0u);
+        const uint4 r1 = draw(g, cg, step, kTagPhantom, 1u);
+        const int k = poisson_inv((double)u01(r.x), g.n_c * phi);
+        nph = (float)k;
+        const float2 zxy = normal2(r.y, r.z);
+        const float zz = normal2(r1.x, r1.y).x;
+        const float sp = g.m * sqrtf(nph * g.kT / g.m);
+        Px = sp * zxy.x;
+        Py = sp * zxy.y;
+        Pz = sp * zz;
+        if (k >= 2) Kint = g.kT * 2.0f * gamma_mt(g, cg, step, kTagPhGamma, 1.5f * (float)(k - 1));
+      }
+      const float ntot = (float)n + nph;
+      const float inv = 1.0f / (g.m * ntot);
+      const float vcx = (g.m * sumx + Px) * inv, vcy = (g.m * sumy + Py) * inv,
+                  vcz = (g.m * sumz + Pz) * inv;
+      const uint4 r = draw(g, cg, step, kTagAxis, 0u);
+      const float ct = 2.0f * u01(r.x) - 1.0f;
+      const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+      float sphi, cphi;
+      sincospif(2.0f * u01(r.y), &sphi, &cphi);
+      float Kph = 0.0f;  // phantom part of sum m |v - v_cm|^2
+      if (nph > 0.0f) {
+        const float dx = Px / (g.m * nph) - vcx, dy = Py / (g.m * nph) - vcy,
+                    dz = Pz / (g.m * nph) - vcz;
+        Kph = Kint + nph * g.m * (dx * dx + dy * dy + dz * dz);
+      }
+      float* P = spar + lc;
+      P[0 * bc] = vcx; P[1 * bc] = vcy; P[2 * bc] = vcz;
+      P[3 * bc] = st * cphi; P[4 * bc] = st * sphi; P[5 * bc] = ct;
+      P[6 * bc] = 1.0f;
+      P[7 * bc] = Kph;
+      P[8 * bc] = ntot;
+      ssum[3 * bc + lc] = 0.0f;
+    } else {
+      const float inv = 1.0f / (float)n;
+      const float* Sm = ssum + lc;
+      const float rcx = Sm[0 * bc] * inv, rcy = Sm[1 * bc] * inv, rcz = Sm[2 * bc] * inv;
+      // second moments M and angular momentum L of w = v - v_ran, about the centre of mass
+      const float Mxx = Sm[6 * bc], Myy = Sm[7 * bc], Mzz = Sm[8 * bc];
+      const float Mxy = Sm[9 * bc], Myz = Sm[10 * bc], Mzx = Sm[11 * bc];
+      const float Lx = Sm[12 * bc], Ly = Sm[13 * bc], Lz = Sm[14 * bc];
+      const float tr = Mxx + Myy + Mzz;
+      float ox_ = 0.0f, oy_ = 0.0f, oz_ = 0.0f;
+      if (n >= 3) {
+        // J = tr(M) 1 - M (moment-of-inertia tensor per unit mass); omega = J^-1 L
+        const float Jxx = tr - Mxx, Jyy = tr - Myy, Jzz = tr - Mzz;
+        const float Jxy = -Mxy, Jyz = -Myz, Jzx = -Mzx;
+        const float A00 = Jyy * Jzz - Jyz * Jyz, A01 = Jzx * Jyz - Jxy * Jzz,
+                    A02 = Jxy * Jyz - Jzx * Jyy, A11 = Jxx * Jzz - Jzx * Jzx,
+                    A12 = Jzx * Jxy - Jxx * Jyz, A22 = Jxx * Jyy - Jxy * Jxy;
+        const float det = Jxx * A00 + Jxy * A01 + Jzx * A02;
+        if (det > 0.0f) {
+          const float id = 1.0f / det;
+          ox_ = (A00 * Lx + A01 * Ly + A02 * Lz) * id;
+          oy_ = (A01 * Lx + A11 * Ly + A12 * Lz) * id;
+          oz_ = (A02 * Lx + A12 * Ly + A22 * Lz) * id;
+        }
+      } else if (n == 2 && tr > 0.0f) {
+        // pair: J = tr(M) (1 - d d^T/|d|^2); pseudo-inverse on the plane normal to d
+        const float it = 1.0f / tr;
+        const float mLx = (Mxx * Lx + Mxy * Ly + Mzx * Lz) * it;
+        const float mLy = (Mxy * Lx + Myy * Ly + Myz * Lz) * it;
+        const float mLz = (Mzx * Lx + Myz * Ly + Mzz * Lz) * it;
+        ox_ = (Lx - mLx) * it;
+        oy_ = (Ly - mLy) * it;
+        oz_ = (Lz - mLz) * it;
+      }
+      float* P = spar + lc;
+      P[0 * bc] = Sm[3 * bc] * inv;
+      P[1 * bc] = Sm[4 * bc] * inv;
+      P[2 * bc] = Sm[5 * bc] * inv;
+      P[3 * bc] = ox_; P[4 * bc] = oy_; P[5 * bc] = oz_;
+      P[6 * bc] = rcx; P[7 * bc] = rcy; P[8 * bc] = rcz;
+    }
+  }
+  __syncthreads();
+
+  if constexpr (VAR == 0) {
+    if (g.thermostat) {
+      // MBS, Eqs. (5)-(7): relative kinetic energy about the final v_cm in a second
+      // pass (no cancellation against the flow velocity), then kappa per cell
+      for (int i = tid; i < cnt; i += kThreads) {
+        const int lc = slc[i];
+        if (lc == 0xFFFF) continue;
+        const float dx = svx[i] - spar[lc], dy = svy[i] - spar[bc + lc], dz = svz[i] - spar[2 * bc + lc];
+        atomicAdd(&ssum[3 * bc + lc], dx * dx + dy * dy + dz * dz);
+      }
+      __syncthreads();
+      for (int lc = tid; lc < bc; lc += kThreads) {
+        const int lx = lc % g.B[0], ly = (lc / g.B[0]) % g.B[1], lz = lc / (g.B[0] * g.B[1]);
+        const int cx = ox + lx, cy = oy + ly, cz = oz + lz;
+        if (cx >= g.Lc[0] || cy >= g.Lc[1] || cz >= g.Lc[2] || scount[lc] == 0) continue;
+        const float ntot = spar[8 * bc + lc];
+        if (ntot < 2.0f) continue;
+        const uint32_t cg = (uint32_t)cx + (uint32_t)g.Lc[0] * ((uint32_t)cy + (uint32_t)g.Lc[1] * (uint32_t)cz);
+        const float Krel = g.m * ssum[3 * bc + lc] + spar[7 * bc + lc];
+        const float Ek = g.kT * gamma_mt(g, cg, step, kTagMbs, 1.5f * (ntot - 1.0f));
+        if (Krel > 0.0f) spar[6 * bc + lc] = sqrtf(2.0f * Ek / Krel);
+      }
+      __syncthreads();
+    }
+  }
+
+  // ---- 4. collide, predict the next cell, count by destination brick ----
+  float o_px = 0, o_py = 0, o_pz = 0, o_e = 0, o_kxy = 0, o_kyz = 0, o_kzx = 0;
+  float o_c[6] = {0, 0, 0, 0, 0, 0};
+  const uint32_t S1x = sh1[0], S1y = sh1[1], S1z = sh1[2];
+  for (int i = tid; i < cnt; i += kThreads) {
+    const uint32_t x = sx[i], y = sy[i], z = sz[i];
+    float vbx = svx[i], vby = svy[i], vbz = svz[i];  // AT+a: w = v - v_ran
+    const int lc = slc[i];
+    float nx = vbx, ny = vby, nz = vbz;
+    if (lc != 0xFFFF) {
+      const float* P = spar + lc;
+      if constexpr (VAR == 0) {
+        const float vcx = P[0], vcy = P[bc], vcz = P[2 * bc];
+        const float ax = P[3 * bc], ay = P[4 * bc], az = P[5 * bc], kap = P[6 * bc];
+        const float rx = vbx - vcx, ry = vby - vcy, rz = vbz - vcz;
+        const float nr = ax * rx + ay * ry + az * rz;
+        const float t = (1.0f - g.cos_a) * nr;
+        nx = vcx + kap * (g.cos_a * rx + g.sin_a * (ay * rz - az * ry) + t * ax);
+        ny = vcy + kap * (g.cos_a * ry + g.sin_a * (az * rx - ax * rz) + t * ay);
+        nz = vcz + kap * (g.cos_a * rz + g.sin_a * (ax * ry - ay * rx) + t * az);
+      } else {
+        const uint4 r = draw(g, sid[i], step, kTagAtVel, 0u);
+        const float2 n01 = normal2(r.x, r.y);
+        const float n2 = normal2(r.z, r.w).x;
+        const float rx = rho_axis(g, x, S0x) - P[6 * bc], ry = rho_axis(g, y, S0y) - P[7 * bc],
+                    rz = rho_axis(g, z, S0z) - P[8 * bc];
+        const float ux = g.sigma * n01.x, uy = g.sigma * n01.y, uz = g.sigma * n2;
+        const float wx = P[3 * bc], wy = P[4 * bc], wz = P[5 * bc];
+        nx = P[0] + ux + (wy * rz - wz * ry);
+        ny = P[bc] + uy + (wz * rx - wx * rz);
+        nz = P[2 * bc] + uz + (wx * ry - wy * rx);
+        vbx += ux; vby += uy; vbz += uz;  // streaming velocity, for the observables
+      }
+    }  // an unbinned particle (error path) keeps the velocity it streamed with
+    if (g.obs) {
+      o_px += nx; o_py += ny; o_pz += nz;
+      o_e += nx * nx + ny * ny + nz * nz;
+      o_kxy += vbx * vby; o_kyz += vby * vbz; o_kzx += vbz * vbx;
+      const float rx = rho_axis(g, x, S0x), ry = rho_axis(g, y, S0y), rz = rho_axis(g, z, S0z);
+      const float dx = nx - vbx, dy = ny - vby, dz = nz - vbz;
+      o_c[0] += dx * ry; o_c[1] += dy * rx; o_c[2] += dy * rz;
+      o_c[3] += dz * ry; o_c[4] += dz * rx; o_c[5] += dx * rz;
+    }
+    svx[i] = nx; svy[i] = ny; svz[i] = nz;
+    // the brick this particle occupies in step n+1
+    uint32_t x2 = x, y2 = y, z2 = z;
+    float ux = nx, uy = ny, uz = nz;
+    stream(g, x2, y2, z2, ux, uy, uz);
+    const int qx = cell_axis(g, x2, S1x, 0) / g.B[0];
+    const int qy = cell_axis(g, y2, S1y, 1) / g.B[1];
+    const int qz = cell_axis(g, z2, S1z, 2) / g.B[2];
+    int dxb, dyb, dzb;
+    dxb = (qx == bx) ? 0 : (qx == (bx + 1) % g.nb[0]) ? 1 : (qx == (bx + g.nb[0] - 1) % g.nb[0]) ? -1 : 9;
+    dyb = (qy == by) ? 0 : (qy == (by + 1) % g.nb[1]) ? 1 : (qy == (by + g.nb[1] - 1) % g.nb[1]) ? -1 : 9;
+    if (g.walls) dzb = (qz == bz) ? 0 : (qz == bz + 1) ? 1 : (qz == bz - 1) ? -1 : 9;
+    else dzb = (qz == bz) ? 0 : (qz == (bz + 1) % g.nb[2]) ? 1 : (qz == (bz + g.nb[2] - 1) % g.nb[2]) ? -1 : 9;
+    uint32_t code = (dxb == 9 || dyb == 9 || dzb == 9) ? 27u : (uint32_t)((dxb + 1) + 3 * (dyb + 1) + 9 * (dzb + 1));
+    const uint32_t rank = atomicAdd(&gcount[code], 1u);
+    saux[i] = code | (rank << 5);
+  }
+  if (g.obs) {
+    const int w = tid >> 5, l = tid & 31;
+    float vals[13] = {o_px, o_py, o_pz, o_e, o_kxy, o_kyz, o_kzx, o_c[0], o_c[1], o_c[2], o_c[3], o_c[4], o_c[5]};
+#pragma unroll
+    for (int q = 0; q < 13; ++q) {
+      const float s = warp_sum(vals[q]);
+      if (l == 0) s_obs[w][q] = s;
+    }
+  }
+  __syncthreads();
+
+  // ---- 5. reserve space in the destination bricks ----
+  if (tid == 0) {
+    uint32_t acc = 0;
+    for (int c = 0; c < 28; ++c) { gstart[c] = acc; acc += gcount[c]; }
+    gstart[28] = acc;
+  }
+  if (tid < 27 && gcount[tid] > 0) {
+    const int dxb = tid % 3 - 1, dyb = (tid / 3) % 3 - 1, dzb = tid / 9 - 1;
+    const int qx = (bx + dxb + g.nb[0]) % g.nb[0];
+    const int qy = (by + dyb + g.nb[1]) % g.nb[1];
+    const int qz = g.walls ? (bz + dzb) : (bz + dzb + g.nb[2]) % g.nb[2];
+    const uint32_t d = (uint32_t)(qx + g.nb[0] * (qy + g.nb[1] * qz));
+    gdest[tid] = d;
+    gbase[tid] = atomicAdd(&cnt_dst[d], gcount[tid]);
+  }
+  if (g.obs && tid < 13) {
+    double s = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) s += (double)s_obs[w][tid];
+    atomicAdd(&a.obs_partials[(b % kObsSlots) * kObsWidth + tid], s);
+  }
+  __syncthreads();
+  for (int i = tid; i < cnt; i += kThreads) {
+    const uint32_t au = saux[i];
+    sperm[gstart[au & 31u] + (au >> 5)] = (uint16_t)i;
+  }
+  __syncthreads();
+
+  // ---- 6. write out, grouped by destination (coalesced within each group) ----
+  for (int t = tid; t < cnt; t += kThreads) {
+    const int i = sperm[t];
+    const uint32_t code = saux[i] & 31u;
+    uint32_t d, slot;
+    if (code < 27) {
+      d = gdest[code];
+      slot = gbase[code] + (uint32_t)t - gstart[code];
+    } else {
+      uint32_t x2 = sx[i], y2 = sy[i], z2 = sz[i];
+      float ux = svx[i], uy = svy[i], uz = svz[i];
+      stream(g, x2, y2, z2, ux, uy, uz);
+      const int qx = cell_axis(g, x2, S1x, 0) / g.B[0];
+      const int qy = cell_axis(g, y2, S1y, 1) / g.B[1];
+      const int qz = cell_axis(g, z2, S1z, 2) / g.B[2];
+      d = (uint32_t)(qx + g.nb[0] * (qy + g.nb[1] * qz));
+      slot = atomicAdd(&cnt_dst[d], 1u);
+    }
+    if (slot < (uint32_t)g.cap) {
+      const size_t o = (size_t)d * g.cap + slot;
+      dst.x[0][o] = sx[i]; dst.x[1][o] = sy[i]; dst.x[2][o] = sz[i];
+      dst.v[0][o] = svx[i]; dst.v[1][o] = svy[i]; dst.v[2][o] = svz[i];
+      dst.id[o] = sid[i];
+      if (g.debug) dst.cell[o] = sgc[i];
+    } else {
+      atomicExch(&a.ctrl->overflow, 1);
+      const uint32_t s = atomicAdd(&a.ctrl->spill_count, 1u);
+      if (s < a.spill.capacity) {
+        a.spill.x[0][s] = sx[i]; a.spill.x[1][s] = sy[i]; a.spill.x[2][s] = sz[i];
+        a.spill.v[0][s] = svx[i]; a.spill.v[1][s] = svy[i]; a.spill.v[2][s] = svz[i];
+        a.spill.id[s] = sid[i];
+        if (g.debug) a.spill.cell[s] = sgc[i];
+        a.spill.dest[s] = d;
+      } else {
+        atomicExch(&a.ctrl->lost, 1);
+      }
+    }
+  }
+}
+
+// Closes a step: reduces the observables partials into the ring, advances the step
+// counter and stops the chain after an overflow.  One block of kObsSlots threads.
+__global__ void k_advance(const StepArgs a) {
+  __shared__ int32_t s_halt;
+  __shared__ int64_t s_step;
+  if (threadIdx.x == 0) {
+    s_halt = *(volatile int32_t*)&a.ctrl->halted;
+    s_step = *(volatile int64_t*)&a.ctrl->step;
+  }
+  __syncthreads();
+  if (s_halt) return;
+  if (a.g.obs) {
+    const int q = threadIdx.x;
+    if (q < kObsWidth) {
+      double s = 0.0;
+      for (int k = 0; k < kObsSlots; ++k) s += a.obs_partials[k * kObsWidth + q];
+      double* row = a.obs_series + (size_t)(s_step % a.obs_ring) * kObsWidth;
+      row[q] = (q == 13) ? (double)(s_step + 1) : s;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < kObsSlots * kObsWidth; k += blockDim.x) a.obs_partials[k] = 0.0;
+  }
+  if (threadIdx.x == 0) {
+    a.ctrl->step = s_step + 1;
+    if (*(volatile int32_t*)&a.ctrl->overflow) a.ctrl->halted = 1;
+  }
+}
+
+size_t step_smem_bytes(const Geom& g) {
+  return g.variant == 0 ? layout_for<0>(g).total : layout_for<1>(g).total;
+}
+
+cudaError_t configure_step_kernels(const Geom& g) {
+  const size_t bytes = step_smem_bytes(g);
+  cudaError_t e = cudaSuccess;
+  if (g.variant == 0)
+    e = cudaFuncSetAttribute(k_step<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  else
+    e = cudaFuncSetAttribute(k_step<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return e;
+}
+
+cudaError_t launch_step(const StepArgs& a, cudaStream_t s) {
+  const size_t bytes = step_smem_bytes(a.g);
+  if (a.g.variant == 0)
+    k_step<0><<<a.g.nbricks, kThreads, bytes, s>>>(a);
+  else
+    k_step<1><<<a.g.nbricks, kThreads, bytes, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance(const StepArgs& a, cudaStream_t s) {
+  k_advance<<<1, kObsSlots, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace mpc

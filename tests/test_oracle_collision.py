@@ -174,3 +174,16 @@ def test_at_a_random_part_variance():
     X, V, ids, obs = oracle.run(p, 30, obs=True)
     T = np.array([o["temperature"] for o in obs[10:]])
     assert abs(T.mean() - kT) < 0.02
+
+
+def test_min_eigenvalue_matches_numpy():
+    """The closed-form smallest eigenvalue (used to scale the float32 parity bound of the
+    angular-momentum variants) against LAPACK."""
+    rng = np.random.default_rng(9)
+    for _ in range(300):
+        A = rng.normal(size=(3, 3))
+        A = A @ A.T * rng.uniform(1e-4, 10)
+        if rng.random() < 0.2:
+            A = np.diag(np.diag(A))
+        ref = np.linalg.eigvalsh(A)[0]
+        assert abs(oracle.min_eigenvalue_sym3(A) - ref) <= 1e-9 * np.abs(A).max()
