@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""MPC step benchmark: particle-steps/s of the fused GB300 step on the MPC-AT+a box of
+512^3 cells, N_c = 10 (1,342,177,280 particles), h = 0.05, kT = 1, periodic.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  `value` is whole-job particle-steps/s with the state
+resident in HBM; `e2e` is the same metric through the public C ABI with the state
+uploaded from pinned host memory, per-step observables read back, and the final state
+downloaded, all inside the timed region.  `roofline` relates the fused step kernel's
+algorithmic bytes (one read and one write of each 28-byte particle) to its live
+CUDA-event duration.  `cpu_baseline` / `--impl reference` time the CPU oracle.
+Under torchrun every rank steps its own independent box (replicas, weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MPC particle-steps/s at 512³·N_c=10, % HBM roofline; batched jobs/s, p99 vs plain"
+UNIT = "particle-steps/s"
+BYTES_PER_PARTICLE = 56  # fused step: read + write of x,y,z (u32), vx,vy,vz (f32), id (u32)
+TWO_SWEEP_MODEL_BYTES = 72  # the two-sweep lower bound of the conventional design
+KERNEL_SOURCES = ["paper_2406_15236_gb300/csrc/mpc_step.cu",
+                  "paper_2406_15236_gb300/csrc/mpc_device.cuh",
+                  "paper_2406_15236_gb300/csrc/mpc_internal.h"]
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_step_at_a.md")
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--L", type=int, default=512)
+    ap.add_argument("--n-c", type=float, default=10.0)
+    ap.add_argument("--variant", choices=["at_a", "srd"], default="at_a")
+    ap.add_argument("--h", type=float, default=0.05)
+    ap.add_argument("--seed", type=int, default=3)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args(argv)
+
+
+def workload(args) -> dict:
+    N = int(round(args.L**3 * args.n_c))
+    name = "MPC-AT+a" if args.variant == "at_a" else "MPC-SRD 130deg"
+    return {"workload": f"{name} periodic box L={args.L} (a=1), N_c={args.n_c:g}, h={args.h:g}, "
+                        f"kT=1, m=1 -> {N:,} particles",
+            "L": args.L, "n_c": args.n_c, "variant": args.variant, "h": args.h, "kT": 1.0,
+            "particles_per_box": N, "seed": args.seed,
+            "l2": "inputs larger than L2 (28 B/particle state in HBM), no flush needed",
+            "parallelism": "replicas"}
+
+
+# --- distributed plumbing -------------------------------------------------------------------
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# --- clocks ------------------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu_index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power)}
+
+
+# --- measured peaks, profile summary ---------------------------------------------------------------
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic_per_particle(variant: str):
+    """DRAM bytes per particle of the step kernel from the committed ncu summary, if it
+    was taken on the current kernel sources (else None)."""
+    try:
+        text = open(PROFILE_SUMMARY).read()
+    except OSError:
+        return None
+    src = re.search(r"source_sha256:\s*([0-9a-f]+)", text)
+    val = re.search(rf"traffic_bytes_per_particle_{variant}:\s*([0-9.]+)", text)
+    if not src or not val or src.group(1) != kernel_source_hash():
+        return None
+    return float(val.group(1))
+
+
+# --- CPU oracle ------------------------------------------------------------------------------------
+
+def _oracle_worker(job):
+    """One process: step an independent oracle box for a bounded time; returns
+    (particles, timed steps, timed seconds)."""
+    import oracle
+
+    L, n_c, variant, h, seed, warm, budget, max_steps = job
+    p = oracle.params(L=L, n_c=n_c, variant=variant, h=h, alpha_deg=130.0, seed=seed)
+    X, V, ids = oracle.init(p)
+    s = 0
+    for _ in range(warm):
+        r = oracle.step(p, X, V, ids, s)
+        X, V = r["X"], r["V"]
+        s += 1
+    t0 = time.perf_counter()
+    n = 0
+    while n < max_steps and (n == 0 or time.perf_counter() - t0 < budget):
+        r = oracle.step(p, X, V, ids, s)
+        X, V = r["X"], r["V"]
+        s += 1
+        n += 1
+    return X.shape[1], n, time.perf_counter() - t0
+
+
+def cpu_oracle_rate(args, budget: float, warm: int = 0, max_steps: int = 10**9, L: int = 32):
+    """The oracle as it stands on every host core (one box per process, spawn pool)."""
+    import multiprocessing as mp
+
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    variant = 1 if args.variant == "at_a" else 0
+    jobs = [(L, args.n_c, variant, args.h, 1000 + k, warm, budget, max_steps) for k in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_worker, jobs)
+    total = sum(n_p * n for n_p, n, _ in res)
+    wall = max(t for _, _, t in res)
+    steps = sum(n for _, n, _ in res)
+    sample = (f"oracle (single-threaded C, FP64) on {cores} processes, each an independent "
+              f"{'AT+a' if variant else 'SRD'} box L={L} N_c={args.n_c:g} h={args.h:g} "
+              f"({res[0][0]:,} particles), {steps} timed steps in total, {wall:.1f} s wall")
+    return total / wall, cores, sample
+
+
+# --- reference arm ---------------------------------------------------------------------------------
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    rate, cores, sample = cpu_oracle_rate(args, budget=1e9, warm=args.warmup,
+                                          max_steps=max(args.steps, 1), L=32)
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload(args),
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --- our arm ----------------------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+
+    from paper_2406_15236_gb300 import _build
+
+    if rank == 0:
+        _build.build()
+    barrier(world)
+    import paper_2406_15236_gb300 as mpc
+
+    variant = mpc.MPC_AT_A if args.variant == "at_a" else mpc.MPC_SRD
+    kw = dict(L=args.L, n_c=args.n_c, h=args.h, alpha_deg=130.0, kT=1.0, variant=variant,
+              seed=args.seed + rank, box_id=rank, flags=mpc.MPC_FLAG_OBSERVABLES)
+    sim = mpc.Simulation(**kw)
+    N = sim.N
+    stream = torch.cuda.current_stream()
+    mpc.mpc_set_profiling(sim.handle, True)
+
+    # warm-up (untimed)
+    sim.step(args.warmup)
+    sim.synchronize()
+    recoveries0 = mpc.mpc_get_info(sim.handle).recoveries
+
+    # --- timed region: K steps, state resident in HBM ---
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.4)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    sim.synchronize()
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if mpc.mpc_get_info(sim.handle).recoveries != recoveries0:
+        # a brick-capacity repair ran after the timed chain stopped: the events did not
+        # cover all K steps, so the number would be wrong
+        raise RuntimeError("capacity repair inside the timed region; rerun")
+    kernel_ms, kernel_samples = mpc.mpc_profile_step_kernel(sim.handle)
+    ms_max = max_over_ranks(ms, world)
+    value = N * world * args.steps / (ms_max / 1e3)
+    obs = sim.observables()
+
+    # --- end to end through the C ABI with host buffers ---
+    e2e = None
+    if not args.no_e2e:
+        mpc.mpc_set_profiling(sim.handle, False)
+        X = torch.empty((3, N), dtype=torch.int32, pin_memory=True)
+        V = torch.empty((3, N), dtype=torch.float32, pin_memory=True)
+        ids = torch.empty(N, dtype=torch.int32, pin_memory=True)
+        mpc.mpc_get_state(sim.handle, X, V, ids)  # a valid state to upload (untimed)
+        rows = 0
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mpc.mpc_set_state(sim.handle, X, V, ids, 0)
+        for _ in range(args.steps):
+            sim.step(1)
+            mpc.mpc_observables(sim.handle)  # device -> host: this step's observables
+            rows += 1
+        mpc.mpc_get_state(sim.handle, X, V, ids)
+        torch.cuda.synchronize()
+        t_e2e = max_over_ranks(time.perf_counter() - t0, world)
+        barrier(world)
+        state_bytes = 28 * N
+        obs_bytes = 16 * 8
+        e2e = {"value": N * world * args.steps / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": state_bytes / args.steps,
+               "d2h_bytes_per_step": (state_bytes + rows * obs_bytes) / args.steps,
+               "note": "state uploaded from pinned host memory, one observables read per step, "
+                       "final state downloaded (sorted by cell), all timed"}
+
+    peak, peak_src = hbm_peak()
+    achieved = BYTES_PER_PARTICLE * N / (kernel_ms / 1e3) / 1e9
+    tpp = profiled_traffic_per_particle(args.variant)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak,
+                "traffic": tpp * N if tpp is not None else None,
+                "kernel": "k_step (fused stream/bin/collide/re-bin), mean of "
+                          f"{kernel_samples} launches in the timed region",
+                "bytes_per_particle": BYTES_PER_PARTICLE, "peak_source": peak_src + ", of measured",
+                "frac_two_sweep_72B_model": value / world * TWO_SWEEP_MODEL_BYTES / 1e9 / peak}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, cores, sample = cpu_oracle_rate(args, budget=args.cpu_seconds, L=32)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic", "config": workload(args), "roofline": roofline,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
+                "clocks": clk,
+                "checks": {"momentum": [float(x) for x in obs["momentum"]],
+                           "temperature": obs["temperature"], "step": obs["step"]}}
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -164,6 +164,14 @@ mpc_status mpc_observable_series(mpc_handle h, double* rows, int64_t count, int6
 
 mpc_status mpc_get_info(mpc_handle h, mpc_info* out);
 
+/* Timing support (no counterpart in the paper beyond its per-partial-step timers,
+ * Fig. 3): when enabled, CUDA events bracket every launch of the fused step kernel on
+ * the handle's stream (inside captured graphs too).  mpc_profile_step_kernel returns
+ * the mean duration in ms over the most recent (up to graph_steps) recorded launches
+ * and the number of launches averaged; it synchronises the stream. */
+mpc_status mpc_set_profiling(mpc_handle h, int enable);
+mpc_status mpc_profile_step_kernel(mpc_handle h, double* mean_ms, int32_t* samples);
+
 /* Text of the last error on h (or of the last failed create when h is NULL). */
 const char* mpc_last_error(mpc_handle h);
 

@@ -96,12 +96,15 @@ def lib():
     L.mpc_observables.argtypes = [vp, P(mpc_obs)]
     L.mpc_observable_series.argtypes = [vp, vp, ctypes.c_int64, P(ctypes.c_int64)]
     L.mpc_get_info.argtypes = [vp, P(mpc_info)]
+    L.mpc_set_profiling.argtypes = [vp, ctypes.c_int]
+    L.mpc_profile_step_kernel.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_int32)]
     L.mpc_last_error.argtypes = [vp]
     L.mpc_last_error.restype = ctypes.c_char_p
     L.mpc_version.restype = ctypes.c_char_p
     for name in ("mpc_create", "mpc_destroy", "mpc_step", "mpc_synchronize", "mpc_get_state",
                  "mpc_set_state", "mpc_get_cell_counts", "mpc_observables",
-                 "mpc_observable_series", "mpc_get_info"):
+                 "mpc_observable_series", "mpc_get_info", "mpc_set_profiling",
+                 "mpc_profile_step_kernel"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -226,6 +229,17 @@ def mpc_get_info(handle) -> mpc_info:
     i = mpc_info()
     _check(lib().mpc_get_info(handle, ctypes.byref(i)), handle)
     return i
+
+
+def mpc_set_profiling(handle, enable: bool) -> None:
+    _check(lib().mpc_set_profiling(handle, int(bool(enable))), handle)
+
+
+def mpc_profile_step_kernel(handle):
+    ms = ctypes.c_double()
+    n = ctypes.c_int32()
+    _check(lib().mpc_profile_step_kernel(handle, ctypes.byref(ms), ctypes.byref(n)), handle)
+    return ms.value, n.value
 
 
 # --- convenience wrapper -----------------------------------------------------------------

@@ -38,6 +38,11 @@ struct mpc_s {
   int graph_steps = 16;
   int recoveries = 0;
   size_t smem_limit = 0;
+  // profiling: event pairs around step-kernel launches (graph nodes and single launches)
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_begin, ev_end;
+  int ev_next = 0;       // next slot for a single launch
+  int ev_recorded = 0;   // valid pairs
   std::string err;
   std::vector<std::pair<void*, size_t>> allocs;
   size_t bytes = 0;
@@ -114,6 +119,16 @@ int ceil_log2(int v) {
   return k;
 }
 
+// derived brick quantities: log2 of the edges, counts, threads per cell
+void finish_bricks(Geom& g) {
+  for (int ax = 0; ax < 3; ++ax) g.Bs[ax] = ceil_log2(g.B[ax]);
+  g.nbricks = g.nb[0] * g.nb[1] * g.nb[2];
+  g.brick_cells = g.B[0] * g.B[1] * g.B[2];
+  int tpc = 1;
+  while (tpc < 32 && tpc * 2 * g.brick_cells <= kStepThreads) tpc *= 2;
+  g.tpc = tpc;
+}
+
 // cells per brick: powers of two, grown on the shortest axis first, ~1280 particles
 void choose_bricks(Geom& g, double n_c) {
   const int target = std::max(1, (int)std::lround(1280.0 / std::max(n_c, 1e-3)));
@@ -129,8 +144,7 @@ void choose_bricks(Geom& g, double n_c) {
     g.B[ax] = B[ax];
     g.nb[ax] = (g.Lc[ax] + B[ax] - 1) / B[ax];
   }
-  g.nbricks = g.nb[0] * g.nb[1] * g.nb[2];
-  g.brick_cells = B[0] * B[1] * B[2];
+  finish_bricks(g);
 }
 
 int capacity_for(double mean) {
@@ -300,7 +314,14 @@ mpc_status build_graph(mpc_handle h) {
   cudaGraph_t graph = nullptr;
   CU(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
   for (int k = 0; k < h->graph_steps; ++k) {
-    cudaError_t e = launch_step(a, h->cap_stream);
+    cudaError_t e = cudaSuccess;
+    // external event-record nodes: recorded each time the graph runs (a plain record
+    // during capture would only express a dependency)
+    if (h->profiling)
+      e = cudaEventRecordWithFlags(h->ev_begin[(size_t)k], h->cap_stream, cudaEventRecordExternal);
+    if (e == cudaSuccess) e = launch_step(a, h->cap_stream);
+    if (e == cudaSuccess && h->profiling)
+      e = cudaEventRecordWithFlags(h->ev_end[(size_t)k], h->cap_stream, cudaEventRecordExternal);
     if (e == cudaSuccess) e = launch_advance(a, h->cap_stream);
     if (e != cudaSuccess) {
       cudaStreamEndCapture(h->cap_stream, &graph);
@@ -323,10 +344,23 @@ mpc_status enqueue_steps(mpc_handle h, int64_t n) {
     while (n >= h->graph_steps) {
       CU(h, cudaGraphLaunch(h->graph, h->stream));
       n -= h->graph_steps;
+      if (h->profiling) {
+        h->ev_recorded = h->graph_steps;
+        h->ev_next = 0;
+      }
     }
   }
   for (int64_t k = 0; k < n; ++k) {
-    CU(h, launch_step(a, h->stream));
+    if (h->profiling) {
+      const size_t slot = (size_t)h->ev_next;
+      CU(h, cudaEventRecord(h->ev_begin[slot], h->stream));
+      CU(h, launch_step(a, h->stream));
+      CU(h, cudaEventRecord(h->ev_end[slot], h->stream));
+      h->ev_next = (h->ev_next + 1) % h->graph_steps;
+      h->ev_recorded = std::min(h->graph_steps, h->ev_recorded + 1);
+    } else {
+      CU(h, launch_step(a, h->stream));
+    }
     CU(h, launch_advance(a, h->stream));
   }
   return MPC_OK;
@@ -501,8 +535,7 @@ mpc_status mpc_create(const mpc_params* p, void* stream, const mpc_allocator* al
         if (g.B[k] > g.B[ax]) ax = k;
       g.B[ax] /= 2;
       g.nb[ax] = (g.Lc[ax] + g.B[ax] - 1) / g.B[ax];
-      g.nbricks = g.nb[0] * g.nb[1] * g.nb[2];
-      g.brick_cells = g.B[0] * g.B[1] * g.B[2];
+      finish_bricks(g);
       g.cap = capacity_for(p->n_c * g.brick_cells);
     }
     if (step_smem_bytes(g) > h->smem_limit)
@@ -556,6 +589,8 @@ mpc_status mpc_destroy(mpc_handle h) {
   cudaSetDevice(h->device);
   cudaStreamSynchronize(h->stream);
   if (h->graph) cudaGraphExecDestroy(h->graph);
+  for (cudaEvent_t e : h->ev_begin) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->ev_end) cudaEventDestroy(e);
   while (!h->allocs.empty()) dev_free(h, h->allocs.back().first);
   if (h->ctrl_host) cudaFreeHost(h->ctrl_host);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -738,6 +773,49 @@ mpc_status mpc_observable_series(mpc_handle h, double* rows, int64_t count, int6
                 sizeof(double) * kObsWidth);
   }
   if (written) *written = n;
+  return MPC_OK;
+}
+
+mpc_status mpc_set_profiling(mpc_handle h, int enable) {
+  if (!h) return fail(nullptr, MPC_EINVAL, "handle is NULL");
+  TRY(set_device(h));
+  const bool on = enable != 0;
+  if (on && h->ev_begin.empty()) {
+    for (int k = 0; k < h->graph_steps; ++k) {
+      cudaEvent_t b, e;
+      CU(h, cudaEventCreate(&b));
+      CU(h, cudaEventCreate(&e));
+      h->ev_begin.push_back(b);
+      h->ev_end.push_back(e);
+    }
+  }
+  if (on != h->profiling) {
+    CU(h, cudaStreamSynchronize(h->stream));
+    if (h->graph) {
+      cudaGraphExecDestroy(h->graph);
+      h->graph = nullptr;
+    }
+    h->profiling = on;
+    h->ev_recorded = 0;
+    h->ev_next = 0;
+  }
+  return MPC_OK;
+}
+
+mpc_status mpc_profile_step_kernel(mpc_handle h, double* mean_ms, int32_t* samples) {
+  if (!h) return fail(nullptr, MPC_EINVAL, "handle is NULL");
+  if (!mean_ms) return fail(h, MPC_EINVAL, "mean_ms is NULL");
+  if (!h->profiling) return fail(h, MPC_ESTATE, "profiling is off");
+  TRY(set_device(h));
+  CU(h, cudaStreamSynchronize(h->stream));
+  double total = 0.0;
+  for (int k = 0; k < h->ev_recorded; ++k) {
+    float ms = 0.0f;
+    CU(h, cudaEventElapsedTime(&ms, h->ev_begin[(size_t)k], h->ev_end[(size_t)k]));
+    total += ms;
+  }
+  *mean_ms = h->ev_recorded ? total / h->ev_recorded : 0.0;
+  if (samples) *samples = h->ev_recorded;
   return MPC_OK;
 }
 

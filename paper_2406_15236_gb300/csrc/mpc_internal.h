@@ -18,11 +18,13 @@ struct Geom {
   float gh[3];       // float32(g h)
   float inv2F;       // 2^-F
   int walls;         // no-slip walls at z = 0, Lz
-  int B[3];          // cells per brick
+  int B[3];          // cells per brick (powers of two)
+  int Bs[3];         // log2 B
   int nb[3];         // bricks per axis
   int nbricks;
   int cap;           // particles per brick buffer
   int brick_cells;   // B[0] B[1] B[2]
+  int tpc;           // threads cooperating on one cell in the finalisation
   int variant;       // 0 SRD, 1 AT+a, 2 SRD+a
   int thermostat;    // MBS after SRD
   float cos_a, sin_a;
@@ -65,6 +67,7 @@ struct Spill {
   uint32_t capacity;
 };
 
+constexpr int kStepThreads = 256;  // threads per CTA of the fused step kernel
 constexpr int kObsSlots = 128;   // partial-sum slots per step (spreads FP64 atomics)
 constexpr int kObsWidth = 16;    // doubles per observables row
 

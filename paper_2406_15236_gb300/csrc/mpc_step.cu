@@ -4,15 +4,18 @@
 // will occupy in the coming step.  For step n a CTA
 //   1. pulls its brick's particles (x, y, z, vx, vy, vz, id: 28 B each) into shared
 //      memory with bulk-async (TMA) copies,
-//   2. streams them (Eq. 1, gravity kick, periodic / bounce-back walls), finds their
-//      cell on the lattice shifted by S(n) (all cells are inside this brick by
-//      construction) and accumulates the per-cell sums with shared-memory atomics,
-//   3. finalises every cell (SRD axis and MBS factor, Eqs. 2 and 5-7, phantom
-//      particles in wall cells; or the AT+a angular velocity),
+//   2. streams them (Eq. 1, gravity kick, periodic / bounce-back walls) and finds their
+//      cell on the lattice shifted by S(n) -- inside this brick by construction -- and
+//      counting-sorts them by cell in shared memory (integer atomics give each
+//      particle its rank in its cell; a scan over the brick's cells gives offsets),
+//   3. finalises every cell from its contiguous member list with register reductions
+//      over a few cooperating threads: SRD axis and MBS factor (Eqs. 2, 5-7) with
+//      phantom particles in wall cells, or the AT+a angular velocity from the moments
+//      about the cell's centre of mass,
 //   4. applies the collision to every particle, predicts the cell of step n+1 from the
-//      streamed position and the new velocity, counting-sorts its particles by
-//      destination brick in shared memory, reserves space in each destination with one
-//      global atomic per (CTA, destination), and writes the particles out coalesced.
+//      streamed position and the new velocity, counting-sorts by destination brick
+//      (warp-aggregated), reserves space in each destination with one global atomic
+//      per (CTA, destination), and writes the particles out coalesced.
 // HBM traffic per particle-step is one read and one write of the 28-byte particle:
 // no global per-cell arrays, no second sweep, no separate reorder pass (the permanent
 // reorder of Sec. III.B.3 happens in every step as part of the write).
@@ -23,32 +26,28 @@
 
 namespace mpc {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = kStepThreads;
 
 template <int VAR>
-struct CellSums;
+struct CellParams;
 template <>
-struct CellSums<0> {
-  // SRD: sum v (3); with the thermostat a second pass adds sum |v - v_cm|^2
-  static constexpr int kSums = 4;
-  // v_cm (3), axis (3), kappa, phantom relative kinetic energy, total count
-  static constexpr int kParams = 9;
+struct CellParams<0> {  // SRD: v_cm (3), rotation axis (3), kappa
+  static constexpr int kParams = 7;
+  static constexpr bool kStoresRandomVelocity = false;
 };
 template <>
-struct CellSums<1> {
-  // AT+a, two passes: sum rho (3), sum w = v - v_ran (3); then, about the cell's centre
-  // of mass, the second moments M = sum r r^T (6) and L = sum r x (w - <w>) (3)
-  static constexpr int kSums = 15;
-  static constexpr int kParams = 9;  // <w> = v_cm - <v_ran> (3), omega (3), rho_cm (3)
+struct CellParams<1> {  // AT+a: <w> = v_cm - <v_ran> (3), omega (3), rho_cm (3)
+  static constexpr int kParams = 9;
+  static constexpr bool kStoresRandomVelocity = true;
 };
 
 struct Layout {
-  size_t x, y, z, vx, vy, vz, id, gcell, lcell, aux, perm, count, sums, params, total;
+  size_t x, y, z, vx, vy, vz, id, gcell, ux, uy, uz, lcr, aux, perm, count, cstart, params, total;
 };
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
-__host__ __device__ inline Layout make_layout(int cap, int bc, int nsums, int nparams, int debug) {
+__host__ __device__ inline Layout make_layout(int cap, int bc, int nparams, bool vran, int debug) {
   Layout L;
   size_t o = 0;
   const size_t a4 = align16(size_t(cap) * 4);
@@ -60,11 +59,14 @@ __host__ __device__ inline Layout make_layout(int cap, int bc, int nsums, int np
   L.vz = o; o += a4;
   L.id = o; o += a4;
   L.gcell = o; o += debug ? a4 : 0;
-  L.lcell = o; o += align16(size_t(cap) * 2);
+  L.ux = o; o += vran ? a4 : 0;
+  L.uy = o; o += vran ? a4 : 0;
+  L.uz = o; o += vran ? a4 : 0;
+  L.lcr = o; o += a4;
   L.aux = o; o += a4;
   L.perm = o; o += align16(size_t(cap) * 2);
   L.count = o; o += align16(size_t(bc) * 4);
-  L.sums = o; o += align16(size_t(bc) * 4 * nsums);
+  L.cstart = o; o += align16(size_t(bc + 1) * 4);
   L.params = o; o += align16(size_t(bc) * 4 * nparams);
   L.total = o;
   return L;
@@ -72,7 +74,8 @@ __host__ __device__ inline Layout make_layout(int cap, int bc, int nsums, int np
 
 template <int VAR>
 __host__ __device__ inline Layout layout_for(const Geom& g) {
-  return make_layout(g.cap, g.brick_cells, CellSums<VAR>::kSums, CellSums<VAR>::kParams, g.debug);
+  return make_layout(g.cap, g.brick_cells, CellParams<VAR>::kParams,
+                     CellParams<VAR>::kStoresRandomVelocity, g.debug);
 }
 
 // --- small PTX wrappers -----------------------------------------------------------
@@ -121,27 +124,48 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// sum over the `tpc` consecutive lanes that cooperate on one cell (tpc a power of two)
+__device__ __forceinline__ float group_sum(float v, int tpc) {
+  for (int o = tpc >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// brick-axis offset of a neighbour: 0 same, +-1 adjacent (with periodic wrap), 9 other
+__device__ __forceinline__ int brick_step(int q, int b, int nb, bool periodic) {
+  if (q == b) return 0;
+  int up = b + 1, dn = b - 1;
+  if (periodic) {
+    if (up == nb) up = 0;
+    if (dn < 0) dn = nb - 1;
+  }
+  if (q == up) return 1;
+  if (q == dn) return -1;
+  return 9;
+}
+
 // --- the step kernel ---------------------------------------------------------------
 template <int VAR>
 __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const Geom& g = a.g;
-  constexpr int NS = CellSums<VAR>::kSums;
   const Layout lay = layout_for<VAR>(g);
 
   uint32_t* sx = reinterpret_cast<uint32_t*>(smem + lay.x);
   uint32_t* sy = reinterpret_cast<uint32_t*>(smem + lay.y);
   uint32_t* sz = reinterpret_cast<uint32_t*>(smem + lay.z);
-  float* svx = reinterpret_cast<float*>(smem + lay.vx);
+  float* svx = reinterpret_cast<float*>(smem + lay.vx);  // SRD: v; AT+a: w = v - v_ran
   float* svy = reinterpret_cast<float*>(smem + lay.vy);
   float* svz = reinterpret_cast<float*>(smem + lay.vz);
   uint32_t* sid = reinterpret_cast<uint32_t*>(smem + lay.id);
   uint32_t* sgc = reinterpret_cast<uint32_t*>(smem + lay.gcell);
-  uint16_t* slc = reinterpret_cast<uint16_t*>(smem + lay.lcell);
-  uint32_t* saux = reinterpret_cast<uint32_t*>(smem + lay.aux);
+  float* sux = reinterpret_cast<float*>(smem + lay.ux);  // AT+a: v_ran
+  float* suy = reinterpret_cast<float*>(smem + lay.uy);
+  float* suz = reinterpret_cast<float*>(smem + lay.uz);
+  uint32_t* slcr = reinterpret_cast<uint32_t*>(smem + lay.lcr);  // local cell | rank << 16
+  uint32_t* saux = reinterpret_cast<uint32_t*>(smem + lay.aux);  // dest code | rank << 5
   uint16_t* sperm = reinterpret_cast<uint16_t*>(smem + lay.perm);
   uint32_t* scount = reinterpret_cast<uint32_t*>(smem + lay.count);
-  float* ssum = reinterpret_cast<float*>(smem + lay.sums);
+  uint32_t* scstart = reinterpret_cast<uint32_t*>(smem + lay.cstart);
   float* spar = reinterpret_cast<float*>(smem + lay.params);
 
   __shared__ __align__(8) uint64_t bar;
@@ -151,6 +175,7 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
   __shared__ float s_obs[kThreads / 32][13];
 
   const int tid = threadIdx.x;
+  const int lane = tid & 31;
   const int b = blockIdx.x;
   const int bc = g.brick_cells;
 
@@ -182,11 +207,7 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
     sh0[0] = s0.x; sh0[1] = s0.y; sh0[2] = s0.z;
     sh1[0] = s1.x; sh1[1] = s1.y; sh1[2] = s1.z;
   }
-  for (int c = tid; c < bc; c += kThreads) {
-    scount[c] = 0;
-#pragma unroll
-    for (int k = 0; k < NS; ++k) ssum[k * bc + c] = 0.0f;
-  }
+  for (int c = tid; c < bc; c += kThreads) scount[c] = 0;
   __syncthreads();
   const int cnt = (int)s_cnt;
   if (tid == 0) {
@@ -212,10 +233,10 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
   const int bx = b % g.nb[0];
   const int by = (b / g.nb[0]) % g.nb[1];
   const int bz = b / (g.nb[0] * g.nb[1]);
-  const int ox = bx * g.B[0], oy = by * g.B[1], oz = bz * g.B[2];
+  const int ox = bx << g.Bs[0], oy = by << g.Bs[1], oz = bz << g.Bs[2];
   const uint32_t S0x = sh0[0], S0y = sh0[1], S0z = sh0[2];
 
-  // ---- 2. stream, bin into the cells of this brick, accumulate cell sums ----
+  // ---- 2. stream and rank each particle within its cell ----
   for (int i = tid; i < cnt; i += kThreads) {
     uint32_t x = sx[i], y = sy[i], z = sz[i];
     float vx = svx[i], vy = svy[i], vz = svz[i];
@@ -223,202 +244,221 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
     const int cx = cell_axis(g, x, S0x, 0), cy = cell_axis(g, y, S0y, 1),
               cz = cell_axis(g, z, S0z, 2);
     const int lx = cx - ox, ly = cy - oy, lz = cz - oz;
-    int lc;
+    uint32_t lcr;
     if ((unsigned)lx < (unsigned)g.B[0] && (unsigned)ly < (unsigned)g.B[1] &&
         (unsigned)lz < (unsigned)g.B[2]) {
-      lc = lx + g.B[0] * (ly + g.B[1] * lz);
+      const uint32_t lc = (uint32_t)(lx | (ly << g.Bs[0]) | (lz << (g.Bs[0] + g.Bs[1])));
+      lcr = lc | (atomicAdd(&scount[lc], 1u) << 16);
     } else {
-      lc = 0xFFFF;  // not binned here: keep the particle, skip its collision
+      lcr = 0xFFFFu;  // not binned here: keep the particle, skip its collision
       atomicOr(&a.ctrl->errors, kErrBinning);
     }
+    slcr[i] = lcr;
     sx[i] = x; sy[i] = y; sz[i] = z;
-    svx[i] = vx; svy[i] = vy; svz[i] = vz;
-    slc[i] = (uint16_t)lc;
     if (g.debug) sgc[i] = (uint32_t)cx + (uint32_t)g.Lc[0] * ((uint32_t)cy + (uint32_t)g.Lc[1] * (uint32_t)cz);
-    if (lc == 0xFFFF) continue;
-    atomicAdd(&scount[lc], 1u);
-    if constexpr (VAR == 0) {
-      atomicAdd(&ssum[0 * bc + lc], vx);
-      atomicAdd(&ssum[1 * bc + lc], vy);
-      atomicAdd(&ssum[2 * bc + lc], vz);
-    } else {
-      // AT+a: w = v - v_ran replaces the velocity in shared memory (v_ran is redrawn
-      // from its Philox key when the collision is applied)
+    if constexpr (VAR == 1) {
+      // AT+a: keep v_ran and w = v - v_ran
       const uint4 r = draw(g, sid[i], step, kTagAtVel, 0u);
       const float2 n01 = normal2(r.x, r.y);
       const float n2 = normal2(r.z, r.w).x;
-      const float wx = vx - g.sigma * n01.x, wy = vy - g.sigma * n01.y, wz = vz - g.sigma * n2;
-      svx[i] = wx; svy[i] = wy; svz[i] = wz;
-      atomicAdd(&ssum[0 * bc + lc], rho_axis(g, x, S0x));
-      atomicAdd(&ssum[1 * bc + lc], rho_axis(g, y, S0y));
-      atomicAdd(&ssum[2 * bc + lc], rho_axis(g, z, S0z));
-      atomicAdd(&ssum[3 * bc + lc], wx);
-      atomicAdd(&ssum[4 * bc + lc], wy);
-      atomicAdd(&ssum[5 * bc + lc], wz);
+      const float ux = g.sigma * n01.x, uy = g.sigma * n01.y, uz = g.sigma * n2;
+      sux[i] = ux; suy[i] = uy; suz[i] = uz;
+      vx -= ux; vy -= uy; vz -= uz;
     }
+    svx[i] = vx; svy[i] = vy; svz[i] = vz;
   }
   __syncthreads();
 
-  if constexpr (VAR == 1) {
-    // second pass: moments about each cell's centre of mass (no cancellation between
-    // a sum of squares and the squared mean, which small cells would suffer)
-    for (int i = tid; i < cnt; i += kThreads) {
-      const int lc = slc[i];
-      if (lc == 0xFFFF) continue;
-      const float inv = 1.0f / (float)scount[lc];
-      const float rx = rho_axis(g, sx[i], S0x) - ssum[0 * bc + lc] * inv;
-      const float ry = rho_axis(g, sy[i], S0y) - ssum[1 * bc + lc] * inv;
-      const float rz = rho_axis(g, sz[i], S0z) - ssum[2 * bc + lc] * inv;
-      const float wx = svx[i] - ssum[3 * bc + lc] * inv;
-      const float wy = svy[i] - ssum[4 * bc + lc] * inv;
-      const float wz = svz[i] - ssum[5 * bc + lc] * inv;
-      atomicAdd(&ssum[6 * bc + lc], rx * rx);
-      atomicAdd(&ssum[7 * bc + lc], ry * ry);
-      atomicAdd(&ssum[8 * bc + lc], rz * rz);
-      atomicAdd(&ssum[9 * bc + lc], rx * ry);
-      atomicAdd(&ssum[10 * bc + lc], ry * rz);
-      atomicAdd(&ssum[11 * bc + lc], rz * rx);
-      atomicAdd(&ssum[12 * bc + lc], ry * wz - rz * wy);
-      atomicAdd(&ssum[13 * bc + lc], rz * wx - rx * wz);
-      atomicAdd(&ssum[14 * bc + lc], rx * wy - ry * wx);
+  // ---- 3a. offsets of the cells' member lists ----
+  if (tid < 32) {
+    const int per = (bc + 31) >> 5;
+    const int c0 = lane * per;
+    uint32_t s = 0;
+    for (int k = 0; k < per; ++k)
+      if (c0 + k < bc) s += scount[c0 + k];
+    uint32_t incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
     }
-    __syncthreads();
+    uint32_t run = incl - s;
+    for (int k = 0; k < per; ++k)
+      if (c0 + k < bc) {
+        scstart[c0 + k] = run;
+        run += scount[c0 + k];
+      }
+    if (lane == 31) scstart[bc] = incl;
   }
+  __syncthreads();
+  for (int i = tid; i < cnt; i += kThreads) {
+    const uint32_t lcr = slcr[i];
+    const uint32_t lc = lcr & 0xFFFFu;
+    if (lc != 0xFFFFu) sperm[scstart[lc] + (lcr >> 16)] = (uint16_t)i;
+  }
+  __syncthreads();
 
-  // ---- 3. finalise every cell of the brick ----
-  for (int lc = tid; lc < bc; lc += kThreads) {
-    const int lx = lc % g.B[0], ly = (lc / g.B[0]) % g.B[1], lz = lc / (g.B[0] * g.B[1]);
-    const int cx = ox + lx, cy = oy + ly, cz = oz + lz;
-    if (cx >= g.Lc[0] || cy >= g.Lc[1] || cz >= g.Lc[2]) continue;
-    const uint32_t cg = (uint32_t)cx + (uint32_t)g.Lc[0] * ((uint32_t)cy + (uint32_t)g.Lc[1] * (uint32_t)cz);
-    const uint32_t n = scount[lc];
-    if (g.debug) a.dbg_counts[cg] = n;
-    if (n == 0) continue;
-    if constexpr (VAR == 0) {
-      const float sumx = ssum[0 * bc + lc], sumy = ssum[1 * bc + lc], sumz = ssum[2 * bc + lc];
-      float nph = 0.0f, Px = 0.0f, Py = 0.0f, Pz = 0.0f, Kint = 0.0f;
-      if (g.walls && (cz == 0 || cz == g.L[2])) {
-        // phantom particles fill the wall part of a cut cell at the mean density
-        // (Sec. II, Boundary conditions): Poisson count, Gaussian momenta, and the
-        // internal kinetic energy of the phantom set ~ kT chi^2(3(n_ph - 1))
-        const double s = (double)sh0[2] * (double)g.inv2F;
-        const double phi = (cz == 0) ? s : 1.0 - s;
-        const uint4 r = draw(g, cg, step, kTagPhantom, 0u);
-        const uint4 r1 = draw(g, cg, step, kTagPhantom, 1u);
-        const int k = poisson_inv((double)u01(r.x), g.n_c * phi);
-        nph = (float)k;
-        const float2 zxy = normal2(r.y, r.z);
-        const float zz = normal2(r1.x, r1.y).x;
-        const float sp = g.m * sqrtf(nph * g.kT / g.m);
-        Px = sp * zxy.x;
-        Py = sp * zxy.y;
-        Pz = sp * zz;
-        if (k >= 2) Kint = g.kT * 2.0f * gamma_mt(g, cg, step, kTagPhGamma, 1.5f * (float)(k - 1));
-      }
-      const float ntot = (float)n + nph;
-      const float inv = 1.0f / (g.m * ntot);
-      const float vcx = (g.m * sumx + Px) * inv, vcy = (g.m * sumy + Py) * inv,
-                  vcz = (g.m * sumz + Pz) * inv;
-      const uint4 r = draw(g, cg, step, kTagAxis, 0u);
-      const float ct = 2.0f * u01(r.x) - 1.0f;
-      const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
-      float sphi, cphi;
-      sincospif(2.0f * u01(r.y), &sphi, &cphi);
-      float Kph = 0.0f;  // phantom part of sum m |v - v_cm|^2
-      if (nph > 0.0f) {
-        const float dx = Px / (g.m * nph) - vcx, dy = Py / (g.m * nph) - vcy,
-                    dz = Pz / (g.m * nph) - vcz;
-        Kph = Kint + nph * g.m * (dx * dx + dy * dy + dz * dz);
-      }
-      float* P = spar + lc;
-      P[0 * bc] = vcx; P[1 * bc] = vcy; P[2 * bc] = vcz;
-      P[3 * bc] = st * cphi; P[4 * bc] = st * sphi; P[5 * bc] = ct;
-      P[6 * bc] = 1.0f;
-      P[7 * bc] = Kph;
-      P[8 * bc] = ntot;
-      ssum[3 * bc + lc] = 0.0f;
-    } else {
-      const float inv = 1.0f / (float)n;
-      const float* Sm = ssum + lc;
-      const float rcx = Sm[0 * bc] * inv, rcy = Sm[1 * bc] * inv, rcz = Sm[2 * bc] * inv;
-      // second moments M and angular momentum L of w = v - v_ran, about the centre of mass
-      const float Mxx = Sm[6 * bc], Myy = Sm[7 * bc], Mzz = Sm[8 * bc];
-      const float Mxy = Sm[9 * bc], Myz = Sm[10 * bc], Mzx = Sm[11 * bc];
-      const float Lx = Sm[12 * bc], Ly = Sm[13 * bc], Lz = Sm[14 * bc];
-      const float tr = Mxx + Myy + Mzz;
-      float ox_ = 0.0f, oy_ = 0.0f, oz_ = 0.0f;
-      if (n >= 3) {
-        // J = tr(M) 1 - M (moment-of-inertia tensor per unit mass); omega = J^-1 L
-        const float Jxx = tr - Mxx, Jyy = tr - Myy, Jzz = tr - Mzz;
-        const float Jxy = -Mxy, Jyz = -Myz, Jzx = -Mzx;
-        const float A00 = Jyy * Jzz - Jyz * Jyz, A01 = Jzx * Jyz - Jxy * Jzz,
-                    A02 = Jxy * Jyz - Jzx * Jyy, A11 = Jxx * Jzz - Jzx * Jzx,
-                    A12 = Jzx * Jxy - Jxx * Jyz, A22 = Jxx * Jyy - Jxy * Jxy;
-        const float det = Jxx * A00 + Jxy * A01 + Jzx * A02;
-        if (det > 0.0f) {
-          const float id = 1.0f / det;
-          ox_ = (A00 * Lx + A01 * Ly + A02 * Lz) * id;
-          oy_ = (A01 * Lx + A11 * Ly + A12 * Lz) * id;
-          oz_ = (A02 * Lx + A12 * Ly + A22 * Lz) * id;
+  // ---- 3b. finalise every cell: `tpc` lanes reduce over its member list ----
+  {
+    const int tpc = g.tpc;
+    const int groups = kThreads / tpc;
+    const int grp = tid / tpc, sub = tid & (tpc - 1);
+    const int leader = lane & ~(tpc - 1);
+    for (int c0 = 0; c0 < bc; c0 += groups) {
+      const int lc = c0 + grp;
+      const int cx = ox + (lc & (g.B[0] - 1));
+      const int cy = oy + ((lc >> g.Bs[0]) & (g.B[1] - 1));
+      const int cz = oz + (lc >> (g.Bs[0] + g.Bs[1]));
+      const bool exists = lc < bc && cx < g.Lc[0] && cy < g.Lc[1] && cz < g.Lc[2];
+      const uint32_t cg = (uint32_t)cx + (uint32_t)g.Lc[0] * ((uint32_t)cy + (uint32_t)g.Lc[1] * (uint32_t)cz);
+      const int n = exists ? (int)scount[lc] : 0;
+      const int base = exists ? (int)scstart[lc] : 0;
+      if (exists && sub == 0 && g.debug) a.dbg_counts[cg] = (uint32_t)n;
+      if constexpr (VAR == 0) {
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+        for (int k = sub; k < n; k += tpc) {
+          const int i = sperm[base + k];
+          s0 += svx[i]; s1 += svy[i]; s2 += svz[i];
         }
-      } else if (n == 2 && tr > 0.0f) {
-        // pair: J = tr(M) (1 - d d^T/|d|^2); pseudo-inverse on the plane normal to d
-        const float it = 1.0f / tr;
-        const float mLx = (Mxx * Lx + Mxy * Ly + Mzx * Lz) * it;
-        const float mLy = (Mxy * Lx + Myy * Ly + Myz * Lz) * it;
-        const float mLz = (Mzx * Lx + Myz * Ly + Mzz * Lz) * it;
-        ox_ = (Lx - mLx) * it;
-        oy_ = (Ly - mLy) * it;
-        oz_ = (Lz - mLz) * it;
+        s0 = group_sum(s0, tpc); s1 = group_sum(s1, tpc); s2 = group_sum(s2, tpc);
+        // phantom particles fill the wall part of a cut cell at the mean density
+        // (Sec. II, Boundary conditions): Poisson count, Gaussian total momentum, and
+        // an internal kinetic energy ~ kT chi^2(3(n_ph - 1)); drawn by the group leader
+        float nph = 0.f, Px = 0.f, Py = 0.f, Pz = 0.f, Kint = 0.f;
+        if (exists && n > 0 && sub == 0 && g.walls && (cz == 0 || cz == g.L[2])) {
+          const double sz_ = (double)S0z * (double)g.inv2F;
+          const double phi = (cz == 0) ? sz_ : 1.0 - sz_;
+          const uint4 r = draw(g, cg, step, kTagPhantom, 0u);
+          const uint4 r1 = draw(g, cg, step, kTagPhantom, 1u);
+          const int k = poisson_inv((double)u01(r.x), g.n_c * phi);
+          nph = (float)k;
+          const float2 zxy = normal2(r.y, r.z);
+          const float zz = normal2(r1.x, r1.y).x;
+          const float sp = g.m * sqrtf(nph * g.kT / g.m);
+          Px = sp * zxy.x; Py = sp * zxy.y; Pz = sp * zz;
+          if (k >= 2) Kint = g.kT * 2.0f * gamma_mt(g, cg, step, kTagPhGamma, 1.5f * (float)(k - 1));
+        }
+        if (tpc > 1) {
+          nph = __shfl_sync(0xffffffffu, nph, leader);
+          Px = __shfl_sync(0xffffffffu, Px, leader);
+          Py = __shfl_sync(0xffffffffu, Py, leader);
+          Pz = __shfl_sync(0xffffffffu, Pz, leader);
+        }
+        const float ntot = (float)n + nph;
+        const float inv = 1.0f / (g.m * fmaxf(ntot, 1.0f));
+        const float vcx = (g.m * s0 + Px) * inv, vcy = (g.m * s1 + Py) * inv,
+                    vcz = (g.m * s2 + Pz) * inv;
+        float kappa = 1.0f;
+        if (g.thermostat) {
+          // MBS, Eqs. (5)-(7): relative kinetic energy about v_cm (second pass)
+          float q = 0.f;
+          for (int k = sub; k < n; k += tpc) {
+            const int i = sperm[base + k];
+            const float dx = svx[i] - vcx, dy = svy[i] - vcy, dz = svz[i] - vcz;
+            q += dx * dx + dy * dy + dz * dz;
+          }
+          q = group_sum(q, tpc);
+          if (exists && n > 0 && sub == 0 && ntot >= 2.0f) {
+            float Krel = g.m * q;
+            if (nph > 0.0f) {
+              const float dx = Px / (g.m * nph) - vcx, dy = Py / (g.m * nph) - vcy,
+                          dz = Pz / (g.m * nph) - vcz;
+              Krel += Kint + nph * g.m * (dx * dx + dy * dy + dz * dz);
+            }
+            const float Ek = g.kT * gamma_mt(g, cg, step, kTagMbs, 1.5f * (ntot - 1.0f));
+            if (Krel > 0.0f) kappa = sqrtf(2.0f * Ek / Krel);
+          }
+        }
+        if (exists && n > 0 && sub == 0) {
+          const uint4 r = draw(g, cg, step, kTagAxis, 0u);
+          const float ct = 2.0f * u01(r.x) - 1.0f;
+          const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+          float sphi, cphi;
+          sincospif(2.0f * u01(r.y), &sphi, &cphi);
+          float* P = spar + lc;
+          P[0 * bc] = vcx; P[1 * bc] = vcy; P[2 * bc] = vcz;
+          P[3 * bc] = st * cphi; P[4 * bc] = st * sphi; P[5 * bc] = ct;
+          P[6 * bc] = kappa;
+        }
+      } else {
+        // AT+a: first pass -- centre of mass and mean w = v - v_ran
+        float r0 = 0.f, r1 = 0.f, r2 = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f;
+        for (int k = sub; k < n; k += tpc) {
+          const int i = sperm[base + k];
+          r0 += rho_axis(g, sx[i], S0x); r1 += rho_axis(g, sy[i], S0y); r2 += rho_axis(g, sz[i], S0z);
+          w0 += svx[i]; w1 += svy[i]; w2 += svz[i];
+        }
+        r0 = group_sum(r0, tpc); r1 = group_sum(r1, tpc); r2 = group_sum(r2, tpc);
+        w0 = group_sum(w0, tpc); w1 = group_sum(w1, tpc); w2 = group_sum(w2, tpc);
+        const float inv = 1.0f / fmaxf((float)n, 1.0f);
+        const float rcx = r0 * inv, rcy = r1 * inv, rcz = r2 * inv;
+        const float wmx = w0 * inv, wmy = w1 * inv, wmz = w2 * inv;
+        // second pass: moments and angular momentum of w about the centre of mass
+        float Mxx = 0.f, Myy = 0.f, Mzz = 0.f, Mxy = 0.f, Myz = 0.f, Mzx = 0.f;
+        float Lx = 0.f, Ly = 0.f, Lz = 0.f;
+        for (int k = sub; k < n; k += tpc) {
+          const int i = sperm[base + k];
+          const float rx = rho_axis(g, sx[i], S0x) - rcx, ry = rho_axis(g, sy[i], S0y) - rcy,
+                      rz = rho_axis(g, sz[i], S0z) - rcz;
+          const float wx = svx[i] - wmx, wy = svy[i] - wmy, wz = svz[i] - wmz;
+          Mxx += rx * rx; Myy += ry * ry; Mzz += rz * rz;
+          Mxy += rx * ry; Myz += ry * rz; Mzx += rz * rx;
+          Lx += ry * wz - rz * wy; Ly += rz * wx - rx * wz; Lz += rx * wy - ry * wx;
+        }
+        Mxx = group_sum(Mxx, tpc); Myy = group_sum(Myy, tpc); Mzz = group_sum(Mzz, tpc);
+        Mxy = group_sum(Mxy, tpc); Myz = group_sum(Myz, tpc); Mzx = group_sum(Mzx, tpc);
+        Lx = group_sum(Lx, tpc); Ly = group_sum(Ly, tpc); Lz = group_sum(Lz, tpc);
+        if (exists && n > 0 && sub == 0) {
+          const float tr = Mxx + Myy + Mzz;
+          float ox_ = 0.0f, oy_ = 0.0f, oz_ = 0.0f;
+          if (n >= 3) {
+            // J = tr(M) 1 - M (moment-of-inertia tensor per unit mass); omega = J^-1 L
+            const float Jxx = tr - Mxx, Jyy = tr - Myy, Jzz = tr - Mzz;
+            const float Jxy = -Mxy, Jyz = -Myz, Jzx = -Mzx;
+            const float A00 = Jyy * Jzz - Jyz * Jyz, A01 = Jzx * Jyz - Jxy * Jzz,
+                        A02 = Jxy * Jyz - Jzx * Jyy, A11 = Jxx * Jzz - Jzx * Jzx,
+                        A12 = Jzx * Jxy - Jxx * Jyz, A22 = Jxx * Jyy - Jxy * Jxy;
+            const float det = Jxx * A00 + Jxy * A01 + Jzx * A02;
+            if (det > 0.0f) {
+              const float id = 1.0f / det;
+              ox_ = (A00 * Lx + A01 * Ly + A02 * Lz) * id;
+              oy_ = (A01 * Lx + A11 * Ly + A12 * Lz) * id;
+              oz_ = (A02 * Lx + A12 * Ly + A22 * Lz) * id;
+            }
+          } else if (n == 2 && tr > 0.0f) {
+            // pair: J = tr(M) (1 - d d^T/|d|^2); pseudo-inverse on the plane normal to d
+            const float it = 1.0f / tr;
+            const float mLx = (Mxx * Lx + Mxy * Ly + Mzx * Lz) * it;
+            const float mLy = (Mxy * Lx + Myy * Ly + Myz * Lz) * it;
+            const float mLz = (Mzx * Lx + Myz * Ly + Mzz * Lz) * it;
+            ox_ = (Lx - mLx) * it;
+            oy_ = (Ly - mLy) * it;
+            oz_ = (Lz - mLz) * it;
+          }
+          float* P = spar + lc;
+          P[0 * bc] = wmx; P[1 * bc] = wmy; P[2 * bc] = wmz;
+          P[3 * bc] = ox_; P[4 * bc] = oy_; P[5 * bc] = oz_;
+          P[6 * bc] = rcx; P[7 * bc] = rcy; P[8 * bc] = rcz;
+        }
       }
-      float* P = spar + lc;
-      P[0 * bc] = Sm[3 * bc] * inv;
-      P[1 * bc] = Sm[4 * bc] * inv;
-      P[2 * bc] = Sm[5 * bc] * inv;
-      P[3 * bc] = ox_; P[4 * bc] = oy_; P[5 * bc] = oz_;
-      P[6 * bc] = rcx; P[7 * bc] = rcy; P[8 * bc] = rcz;
     }
   }
   __syncthreads();
-
-  if constexpr (VAR == 0) {
-    if (g.thermostat) {
-      // MBS, Eqs. (5)-(7): relative kinetic energy about the final v_cm in a second
-      // pass (no cancellation against the flow velocity), then kappa per cell
-      for (int i = tid; i < cnt; i += kThreads) {
-        const int lc = slc[i];
-        if (lc == 0xFFFF) continue;
-        const float dx = svx[i] - spar[lc], dy = svy[i] - spar[bc + lc], dz = svz[i] - spar[2 * bc + lc];
-        atomicAdd(&ssum[3 * bc + lc], dx * dx + dy * dy + dz * dz);
-      }
-      __syncthreads();
-      for (int lc = tid; lc < bc; lc += kThreads) {
-        const int lx = lc % g.B[0], ly = (lc / g.B[0]) % g.B[1], lz = lc / (g.B[0] * g.B[1]);
-        const int cx = ox + lx, cy = oy + ly, cz = oz + lz;
-        if (cx >= g.Lc[0] || cy >= g.Lc[1] || cz >= g.Lc[2] || scount[lc] == 0) continue;
-        const float ntot = spar[8 * bc + lc];
-        if (ntot < 2.0f) continue;
-        const uint32_t cg = (uint32_t)cx + (uint32_t)g.Lc[0] * ((uint32_t)cy + (uint32_t)g.Lc[1] * (uint32_t)cz);
-        const float Krel = g.m * ssum[3 * bc + lc] + spar[7 * bc + lc];
-        const float Ek = g.kT * gamma_mt(g, cg, step, kTagMbs, 1.5f * (ntot - 1.0f));
-        if (Krel > 0.0f) spar[6 * bc + lc] = sqrtf(2.0f * Ek / Krel);
-      }
-      __syncthreads();
-    }
-  }
 
   // ---- 4. collide, predict the next cell, count by destination brick ----
   float o_px = 0, o_py = 0, o_pz = 0, o_e = 0, o_kxy = 0, o_kyz = 0, o_kzx = 0;
   float o_c[6] = {0, 0, 0, 0, 0, 0};
   const uint32_t S1x = sh1[0], S1y = sh1[1], S1z = sh1[2];
+  const bool zper = !g.walls;
   for (int i = tid; i < cnt; i += kThreads) {
     const uint32_t x = sx[i], y = sy[i], z = sz[i];
-    float vbx = svx[i], vby = svy[i], vbz = svz[i];  // AT+a: w = v - v_ran
-    const int lc = slc[i];
-    float nx = vbx, ny = vby, nz = vbz;
-    if (lc != 0xFFFF) {
-      const float* P = spar + lc;
-      if constexpr (VAR == 0) {
+    float vbx = svx[i], vby = svy[i], vbz = svz[i];  // AT+a: w
+    const uint32_t lc = slcr[i] & 0xFFFFu;
+    float nx, ny, nz;
+    if constexpr (VAR == 0) {
+      nx = vbx; ny = vby; nz = vbz;
+      if (lc != 0xFFFFu) {
+        const float* P = spar + lc;
         const float vcx = P[0], vcy = P[bc], vcz = P[2 * bc];
         const float ax = P[3 * bc], ay = P[4 * bc], az = P[5 * bc], kap = P[6 * bc];
         const float rx = vbx - vcx, ry = vby - vcy, rz = vbz - vcz;
@@ -427,20 +467,21 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
         nx = vcx + kap * (g.cos_a * rx + g.sin_a * (ay * rz - az * ry) + t * ax);
         ny = vcy + kap * (g.cos_a * ry + g.sin_a * (az * rx - ax * rz) + t * ay);
         nz = vcz + kap * (g.cos_a * rz + g.sin_a * (ax * ry - ay * rx) + t * az);
-      } else {
-        const uint4 r = draw(g, sid[i], step, kTagAtVel, 0u);
-        const float2 n01 = normal2(r.x, r.y);
-        const float n2 = normal2(r.z, r.w).x;
+      }
+    } else {
+      const float ux = sux[i], uy = suy[i], uz = suz[i];
+      vbx += ux; vby += uy; vbz += uz;  // the velocity the particle streamed with
+      nx = vbx; ny = vby; nz = vbz;
+      if (lc != 0xFFFFu) {
+        const float* P = spar + lc;
         const float rx = rho_axis(g, x, S0x) - P[6 * bc], ry = rho_axis(g, y, S0y) - P[7 * bc],
                     rz = rho_axis(g, z, S0z) - P[8 * bc];
-        const float ux = g.sigma * n01.x, uy = g.sigma * n01.y, uz = g.sigma * n2;
         const float wx = P[3 * bc], wy = P[4 * bc], wz = P[5 * bc];
         nx = P[0] + ux + (wy * rz - wz * ry);
         ny = P[bc] + uy + (wz * rx - wx * rz);
         nz = P[2 * bc] + uz + (wx * ry - wy * rx);
-        vbx += ux; vby += uy; vbz += uz;  // streaming velocity, for the observables
       }
-    }  // an unbinned particle (error path) keeps the velocity it streamed with
+    }
     if (g.obs) {
       o_px += nx; o_py += ny; o_pz += nz;
       o_e += nx * nx + ny * ny + nz * nz;
@@ -453,27 +494,34 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
     svx[i] = nx; svy[i] = ny; svz[i] = nz;
     // the brick this particle occupies in step n+1
     uint32_t x2 = x, y2 = y, z2 = z;
-    float ux = nx, uy = ny, uz = nz;
-    stream(g, x2, y2, z2, ux, uy, uz);
-    const int qx = cell_axis(g, x2, S1x, 0) / g.B[0];
-    const int qy = cell_axis(g, y2, S1y, 1) / g.B[1];
-    const int qz = cell_axis(g, z2, S1z, 2) / g.B[2];
-    int dxb, dyb, dzb;
-    dxb = (qx == bx) ? 0 : (qx == (bx + 1) % g.nb[0]) ? 1 : (qx == (bx + g.nb[0] - 1) % g.nb[0]) ? -1 : 9;
-    dyb = (qy == by) ? 0 : (qy == (by + 1) % g.nb[1]) ? 1 : (qy == (by + g.nb[1] - 1) % g.nb[1]) ? -1 : 9;
-    if (g.walls) dzb = (qz == bz) ? 0 : (qz == bz + 1) ? 1 : (qz == bz - 1) ? -1 : 9;
-    else dzb = (qz == bz) ? 0 : (qz == (bz + 1) % g.nb[2]) ? 1 : (qz == (bz + g.nb[2] - 1) % g.nb[2]) ? -1 : 9;
-    uint32_t code = (dxb == 9 || dyb == 9 || dzb == 9) ? 27u : (uint32_t)((dxb + 1) + 3 * (dyb + 1) + 9 * (dzb + 1));
-    const uint32_t rank = atomicAdd(&gcount[code], 1u);
+    float ux2 = nx, uy2 = ny, uz2 = nz;
+    stream(g, x2, y2, z2, ux2, uy2, uz2);
+    const int qx = cell_axis(g, x2, S1x, 0) >> g.Bs[0];
+    const int qy = cell_axis(g, y2, S1y, 1) >> g.Bs[1];
+    const int qz = cell_axis(g, z2, S1z, 2) >> g.Bs[2];
+    const int dxb = brick_step(qx, bx, g.nb[0], true);
+    const int dyb = brick_step(qy, by, g.nb[1], true);
+    const int dzb = brick_step(qz, bz, g.nb[2], zper);
+    const uint32_t code = (dxb == 9 || dyb == 9 || dzb == 9)
+                              ? 27u
+                              : (uint32_t)((dxb + 1) + 3 * (dyb + 1) + 9 * (dzb + 1));
+    // warp-aggregated rank within the destination group
+    const uint32_t active = __activemask();
+    const uint32_t peers = __match_any_sync(active, code);
+    const int first = __ffs(peers) - 1;
+    uint32_t rank0 = 0;
+    if (lane == first) rank0 = atomicAdd(&gcount[code], (uint32_t)__popc(peers));
+    rank0 = __shfl_sync(peers, rank0, first);
+    const uint32_t rank = rank0 + (uint32_t)__popc(peers & ((1u << lane) - 1u));
     saux[i] = code | (rank << 5);
   }
   if (g.obs) {
-    const int w = tid >> 5, l = tid & 31;
+    const int w = tid >> 5;
     float vals[13] = {o_px, o_py, o_pz, o_e, o_kxy, o_kyz, o_kzx, o_c[0], o_c[1], o_c[2], o_c[3], o_c[4], o_c[5]};
 #pragma unroll
     for (int q = 0; q < 13; ++q) {
       const float s = warp_sum(vals[q]);
-      if (l == 0) s_obs[w][q] = s;
+      if (lane == 0) s_obs[w][q] = s;
     }
   }
   __syncthreads();
@@ -486,9 +534,10 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
   }
   if (tid < 27 && gcount[tid] > 0) {
     const int dxb = tid % 3 - 1, dyb = (tid / 3) % 3 - 1, dzb = tid / 9 - 1;
-    const int qx = (bx + dxb + g.nb[0]) % g.nb[0];
-    const int qy = (by + dyb + g.nb[1]) % g.nb[1];
-    const int qz = g.walls ? (bz + dzb) : (bz + dzb + g.nb[2]) % g.nb[2];
+    int qx = bx + dxb, qy = by + dyb, qz = bz + dzb;
+    if (qx < 0) qx += g.nb[0]; else if (qx >= g.nb[0]) qx -= g.nb[0];
+    if (qy < 0) qy += g.nb[1]; else if (qy >= g.nb[1]) qy -= g.nb[1];
+    if (zper) { if (qz < 0) qz += g.nb[2]; else if (qz >= g.nb[2]) qz -= g.nb[2]; }
     const uint32_t d = (uint32_t)(qx + g.nb[0] * (qy + g.nb[1] * qz));
     gdest[tid] = d;
     gbase[tid] = atomicAdd(&cnt_dst[d], gcount[tid]);
@@ -517,9 +566,9 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
       uint32_t x2 = sx[i], y2 = sy[i], z2 = sz[i];
       float ux = svx[i], uy = svy[i], uz = svz[i];
       stream(g, x2, y2, z2, ux, uy, uz);
-      const int qx = cell_axis(g, x2, S1x, 0) / g.B[0];
-      const int qy = cell_axis(g, y2, S1y, 1) / g.B[1];
-      const int qz = cell_axis(g, z2, S1z, 2) / g.B[2];
+      const int qx = cell_axis(g, x2, S1x, 0) >> g.Bs[0];
+      const int qy = cell_axis(g, y2, S1y, 1) >> g.Bs[1];
+      const int qz = cell_axis(g, z2, S1z, 2) >> g.Bs[2];
       d = (uint32_t)(qx + g.nb[0] * (qy + g.nb[1] * qz));
       slot = atomicAdd(&cnt_dst[d], 1u);
     }
