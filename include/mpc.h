@@ -172,6 +172,27 @@ mpc_status mpc_get_info(mpc_handle h, mpc_info* out);
 mpc_status mpc_set_profiling(mpc_handle h, int enable);
 mpc_status mpc_profile_step_kernel(mpc_handle h, double* mean_ms, int32_t* samples);
 
+/* Checkpoint ordering without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory when they need
+ * it -- e.g. a serving loop whose memory pool owns all of HBM, or code that must not
+ * trigger the device-wide synchronisation of cudaFree while other streams run.
+ * It sorts n particles by unshifted cell index (the order mpc_get_state produces;
+ * arbitrary order inside a cell) using only the caller's arrays plus a fixed scratch
+ * area compiled into the library (8.4 MB per device, held until the process exits).
+ * L: box edges (each in [2, 1024]) with Lx Ly Lz <= 2,097,152 cells, else MPC_EINVAL.
+ * X, V (3n each, SoA, the state contract above), id (n) or NULL: device inputs;
+ * X_out, V_out, id_out (NULL exactly when id is NULL): device outputs, not aliasing the
+ * inputs.  Positions outside [0, L << F) are rejected with MPC_EINVAL before sorting.
+ * stream: cudaStream_t or NULL; the call synchronises it before returning.
+ * The first call on a device looks up the scratch area's device address for that
+ * device (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls in the process share the one scratch area: calls that overlap on the GPU
+ * (different streams or threads, not ordered) race and corrupt each other's results.
+ * Errors are reported through mpc_last_error(NULL). */
+mpc_status mpc_sort_by_cell_noalloc(const int32_t L[3], int64_t n, const uint32_t* X,
+                                    const float* V, const uint32_t* id, uint32_t* X_out,
+                                    float* V_out, uint32_t* id_out, void* stream);
+
 /* Text of the last error on h (or of the last failed create when h is NULL). */
 const char* mpc_last_error(mpc_handle h);
 

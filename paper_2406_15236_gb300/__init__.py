@@ -98,13 +98,15 @@ def lib():
     L.mpc_get_info.argtypes = [vp, P(mpc_info)]
     L.mpc_set_profiling.argtypes = [vp, ctypes.c_int]
     L.mpc_profile_step_kernel.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_int32)]
+    L.mpc_sort_by_cell_noalloc.argtypes = [P(ctypes.c_int32), ctypes.c_int64, vp, vp, vp, vp, vp,
+                                           vp, vp]
     L.mpc_last_error.argtypes = [vp]
     L.mpc_last_error.restype = ctypes.c_char_p
     L.mpc_version.restype = ctypes.c_char_p
     for name in ("mpc_create", "mpc_destroy", "mpc_step", "mpc_synchronize", "mpc_get_state",
                  "mpc_set_state", "mpc_get_cell_counts", "mpc_observables",
                  "mpc_observable_series", "mpc_get_info", "mpc_set_profiling",
-                 "mpc_profile_step_kernel"):
+                 "mpc_profile_step_kernel", "mpc_sort_by_cell_noalloc"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -240,6 +242,16 @@ def mpc_profile_step_kernel(handle):
     n = ctypes.c_int32()
     _check(lib().mpc_profile_step_kernel(handle, ctypes.byref(ms), ctypes.byref(n)), handle)
     return ms.value, n.value
+
+
+def mpc_sort_by_cell_noalloc(L, n, X, V, ids, X_out, V_out, ids_out, stream=None) -> None:
+    """Sort n particles (device arrays) by unshifted cell without allocating device
+    memory; see include/mpc.h for who needs this and its limits."""
+    if isinstance(L, int):
+        L = (L, L, L)
+    Lc = (ctypes.c_int32 * 3)(*L)
+    _check(lib().mpc_sort_by_cell_noalloc(Lc, int(n), _addr(X), _addr(V), _addr(ids), _addr(X_out),
+                                          _addr(V_out), _addr(ids_out), ctypes.c_void_p(stream or 0)))
 
 
 # --- convenience wrapper -----------------------------------------------------------------

@@ -454,6 +454,11 @@ mpc_status set_device(mpc_handle h) {
 
 }  // namespace
 
+namespace mpc {
+// lets entry points that take no handle report through mpc_last_error(NULL)
+void set_null_handle_error(const std::string& msg) { g_last_create_error = msg; }
+}  // namespace mpc
+
 extern "C" {
 
 const char* mpc_version(void) { return kVersion; }
