@@ -398,6 +398,7 @@ mpc_status gather(mpc_handle h, Staging& st, bool with_cell) {
   Spill sp = h->spill;
   if (!with_cell) sp.cell = nullptr;
   CU(h, launch_append_spill(sp, spill, total, st.b, h->stream));
+  CU(h, launch_unstream(g, h->N, st.b, h->stream));
   CU(h, cudaStreamSynchronize(h->stream));
   dev_free(h, offs);
   return MPC_OK;

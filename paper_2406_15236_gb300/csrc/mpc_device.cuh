@@ -110,10 +110,11 @@ __device__ __forceinline__ int displacement(float v, float hs, uint32_t P) {
   return max(-lim, min(lim, d));
 }
 
-__device__ __forceinline__ uint32_t wrap(int64_t t, uint32_t P) {
-  if (t < 0) t += (int64_t)P;
-  else if (t >= (int64_t)P) t -= (int64_t)P;
-  return (uint32_t)t;
+// (x + d) mod P for x in [0, P), |d| <= P - 1, P <= 2^31, in 32-bit arithmetic
+__device__ __forceinline__ uint32_t add_wrap(uint32_t x, int d, uint32_t P) {
+  uint32_t t = x + (uint32_t)d;
+  if (t >= P) t = (d < 0) ? t + P : t - P;
+  return t;
 }
 
 // round(num / den) to nearest, ties to even, exact integers (den != 0)
@@ -126,10 +127,15 @@ __device__ __forceinline__ int64_t rdiv_half_even(int64_t num, int64_t den) {
   return q;
 }
 
-// Eq. (1) with gravity kick and boundary conditions.  (x, v) in; x out is the streamed
-// position, v out the velocity entering the collision (reversed after a wall hit).
+// Stored positions carry, in bit 31 of z (positions are below 2^31), whether the
+// streaming that produced them crossed a wall.
+constexpr uint32_t kCrossedBit = 0x80000000u;
+
+// Eq. (1) with gravity kick and boundary conditions.  In: position x and velocity v
+// before the step.  Out: the streamed position (z with kCrossedBit set after a wall
+// hit).  The velocity entering the collision is (crossed ? -1 : 1) * (v + g h).
 __device__ __forceinline__ void stream(const Geom& g, uint32_t& x, uint32_t& y, uint32_t& z,
-                                       float& vx, float& vy, float& vz) {
+                                       float vx, float vy, float vz) {
   vx = __fadd_rn(vx, g.gh[0]);
   vy = __fadd_rn(vy, g.gh[1]);
   vz = __fadd_rn(vz, g.gh[2]);
@@ -144,18 +150,58 @@ __device__ __forceinline__ void stream(const Geom& g, uint32_t& x, uint32_t& y, 
       const int64_t Znew = (zn >= Pz) ? (2 * Pz - 1 - zn) : (-1 - zn);
       dx = (int)rdiv_half_even((int64_t)dx * (Znew - Z), (int64_t)dz);
       dy = (int)rdiv_half_even((int64_t)dy * (Znew - Z), (int64_t)dz);
-      z = (uint32_t)Znew;
-      vx = -vx;
-      vy = -vy;
-      vz = -vz;
+      z = (uint32_t)Znew | kCrossedBit;
     } else {
       z = (uint32_t)zn;
     }
   } else {
-    z = wrap((int64_t)z + dz, g.P[2]);
+    z = add_wrap(z, dz, g.P[2]);
   }
-  x = wrap((int64_t)x + dx, g.P[0]);
-  y = wrap((int64_t)y + dy, g.P[1]);
+  x = add_wrap(x, dx, g.P[0]);
+  y = add_wrap(y, dy, g.P[1]);
+}
+
+// The exact inverse of stream(): from a stored (streamed) position and the velocity v it
+// was streamed with (before the kick), the position before the step.
+__device__ __forceinline__ void unstream(const Geom& g, uint32_t& x, uint32_t& y, uint32_t& z,
+                                         float vx, float vy, float vz) {
+  vx = __fadd_rn(vx, g.gh[0]);
+  vy = __fadd_rn(vy, g.gh[1]);
+  vz = __fadd_rn(vz, g.gh[2]);
+  int dx = displacement(vx, g.hs, g.P[0]);
+  int dy = displacement(vy, g.hs, g.P[1]);
+  const int dz = displacement(vz, g.hs, g.P[2]);
+  const bool crossed = (z & kCrossedBit) != 0;
+  const uint32_t zs = z & ~kCrossedBit;
+  if (g.walls) {
+    if (crossed) {
+      const int64_t Pz = g.P[2];
+      const int64_t zn = (dz > 0) ? (2 * Pz - 1 - (int64_t)zs) : (-1 - (int64_t)zs);
+      const int64_t Z = zn - dz;
+      dx = (int)rdiv_half_even((int64_t)dx * ((int64_t)zs - Z), (int64_t)dz);
+      dy = (int)rdiv_half_even((int64_t)dy * ((int64_t)zs - Z), (int64_t)dz);
+      z = (uint32_t)Z;
+    } else {
+      z = zs - (uint32_t)dz;
+    }
+  } else {
+    z = add_wrap(zs, -dz, g.P[2]);
+  }
+  x = add_wrap(x, -dx, g.P[0]);
+  y = add_wrap(y, -dy, g.P[1]);
+}
+
+// velocity entering the collision for a particle stored as (streamed x, pre-kick v)
+__device__ __forceinline__ void collision_velocity(const Geom& g, uint32_t zraw, float& vx, float& vy,
+                                                   float& vz) {
+  vx = __fadd_rn(vx, g.gh[0]);
+  vy = __fadd_rn(vy, g.gh[1]);
+  vz = __fadd_rn(vz, g.gh[2]);
+  if (zraw & kCrossedBit) {
+    vx = -vx;
+    vy = -vy;
+    vz = -vz;
+  }
 }
 
 // cell of the shifted lattice, per axis; periodic axes wrap index L to 0

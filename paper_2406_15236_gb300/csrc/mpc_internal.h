@@ -109,6 +109,8 @@ cudaError_t launch_compact(const Geom& g, const PBuf& src, const uint32_t* cnt,
                            const uint32_t* offsets, const PBuf& dst, cudaStream_t s);
 cudaError_t launch_append_spill(const Spill& sp, uint32_t count, uint64_t base, const PBuf& dst,
                                 cudaStream_t s);
+// bricks hold streamed positions; converts a gathered set back to the state contract
+cudaError_t launch_unstream(const Geom& g, int64_t N, const PBuf& b, cudaStream_t s);
 cudaError_t launch_cell_hist(const Geom& g, int64_t N, uint32_t* const x[3], uint32_t* hist,
                              cudaStream_t s);
 cudaError_t launch_cell_scatter(const Geom& g, int64_t N, const PBuf& src, uint32_t* cursor,

@@ -32,13 +32,14 @@ __device__ __forceinline__ uint32_t aggregated_inc(uint32_t* counter, uint32_t k
   return base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
 }
 
-// brick of the collision cell a particle occupies in step `step`
-__device__ __forceinline__ uint32_t brick_of(const Geom& g, uint32_t x, uint32_t y, uint32_t z, float vx,
-                                             float vy, float vz, uint3 S, uint32_t* gcell) {
+// streams a particle for step `step` (in place) and returns the brick of its collision
+// cell in that step
+__device__ __forceinline__ uint32_t stream_to_brick(const Geom& g, uint32_t& x, uint32_t& y, uint32_t& z,
+                                                    float vx, float vy, float vz, uint3 S) {
   stream(g, x, y, z, vx, vy, vz);
-  const int cx = cell_axis(g, x, S.x, 0), cy = cell_axis(g, y, S.y, 1), cz = cell_axis(g, z, S.z, 2);
-  if (gcell) *gcell = (uint32_t)cx + (uint32_t)g.Lc[0] * ((uint32_t)cy + (uint32_t)g.Lc[1] * (uint32_t)cz);
-  return (uint32_t)(cx / g.B[0] + g.nb[0] * (cy / g.B[1] + g.nb[1] * (cz / g.B[2])));
+  const int cx = cell_axis(g, x, S.x, 0), cy = cell_axis(g, y, S.y, 1),
+            cz = cell_axis(g, z & ~kCrossedBit, S.z, 2);
+  return (uint32_t)((cx >> g.Bs[0]) + g.nb[0] * ((cy >> g.Bs[1]) + g.nb[1] * (cz >> g.Bs[2])));
 }
 
 __global__ void k_init_particles(const Geom g, int64_t N, uint32_t* x0, uint32_t* x1, uint32_t* x2,
@@ -103,7 +104,8 @@ __global__ void k_bin_count(const Geom g, int64_t N, const uint32_t* x0, const u
     return;
   }
   const uint3 S = lattice_shift(g, step);
-  const uint32_t b = brick_of(g, x0[i], x1[i], x2[i], v0[i], v1[i], v2[i], S, nullptr);
+  uint32_t x = x0[i], y = x1[i], z = x2[i];
+  const uint32_t b = stream_to_brick(g, x, y, z, v0[i], v1[i], v2[i], S);
   aggregated_inc(counts, b);
 }
 
@@ -114,14 +116,16 @@ __global__ void k_bin_scatter(const Geom g, int64_t N, const uint32_t* x0, const
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const uint3 S = lattice_shift(g, step);
-  const uint32_t b = brick_of(g, x0[i], x1[i], x2[i], v0[i], v1[i], v2[i], S, nullptr);
+  uint32_t x = x0[i], y = x1[i], z = x2[i];
+  const uint32_t b = stream_to_brick(g, x, y, z, v0[i], v1[i], v2[i], S);
   const uint32_t slot = aggregated_inc(cnt, b);
   if (slot >= (uint32_t)g.cap) {
     atomicOr(errors, kErrRange);
     return;
   }
+  // bricks hold positions already streamed for the coming step (see mpc_step.cu)
   const size_t o = (size_t)b * g.cap + slot;
-  dst.x[0][o] = x0[i]; dst.x[1][o] = x1[i]; dst.x[2][o] = x2[i];
+  dst.x[0][o] = x; dst.x[1][o] = y; dst.x[2][o] = z;
   dst.v[0][o] = v0[i]; dst.v[1][o] = v1[i]; dst.v[2][o] = v2[i];
   dst.id[o] = id[i];
   if (dst.cell) dst.cell[o] = cell ? cell[i] : 0xFFFFFFFFu;
@@ -224,6 +228,15 @@ __global__ void k_append_spill(Spill sp, uint32_t count, uint64_t base, PBuf dst
   dst.v[0][o] = sp.v[0][k]; dst.v[1][o] = sp.v[1][k]; dst.v[2][o] = sp.v[2][k];
   dst.id[o] = sp.id[k];
   if (dst.cell && sp.cell) dst.cell[o] = sp.cell[k];
+}
+
+// bricks store streamed positions: back to the state before the coming step
+__global__ void k_unstream(const Geom g, int64_t N, PBuf b) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  uint32_t x = b.x[0][i], y = b.x[1][i], z = b.x[2][i];
+  unstream(g, x, y, z, b.v[0][i], b.v[1][i], b.v[2][i]);
+  b.x[0][i] = x; b.x[1][i] = y; b.x[2][i] = z;
 }
 
 __device__ __forceinline__ uint32_t unshifted_cell(const Geom& g, uint32_t x, uint32_t y, uint32_t z) {
@@ -348,6 +361,12 @@ cudaError_t launch_append_spill(const Spill& sp, uint32_t count, uint64_t base, 
                                 cudaStream_t s) {
   if (count == 0) return cudaSuccess;
   k_append_spill<<<grid_for(count), kBlock, 0, s>>>(sp, count, base, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unstream(const Geom& g, int64_t N, const PBuf& b, cudaStream_t s) {
+  if (N <= 0) return cudaSuccess;
+  k_unstream<<<grid_for(N), kBlock, 0, s>>>(g, N, b);
   return cudaGetLastError();
 }
 

@@ -1,21 +1,23 @@
 // The fused MPC step: one CTA per brick of collision cells.
 //
 // Particles live in fixed-capacity brick buffers, binned by the collision cell they
-// will occupy in the coming step.  For step n a CTA
+// will occupy in the coming step, with their positions already streamed for that step
+// (Eq. 1 with gravity kick and periodic / bounce-back walls; a wall crossing is kept in
+// bit 31 of z) and the velocity they streamed with.  For step n a CTA
 //   1. pulls its brick's particles (x, y, z, vx, vy, vz, id: 28 B each) into shared
 //      memory with bulk-async (TMA) copies,
-//   2. streams them (Eq. 1, gravity kick, periodic / bounce-back walls) and finds their
-//      cell on the lattice shifted by S(n) -- inside this brick by construction -- and
-//      counting-sorts them by cell in shared memory (integer atomics give each
-//      particle its rank in its cell; a scan over the brick's cells gives offsets),
+//   2. finds their cell on the lattice shifted by S(n) -- inside this brick by
+//      construction -- and counting-sorts them by cell in shared memory (integer
+//      atomics give each particle its rank in its cell; a scan gives offsets),
 //   3. finalises every cell from its contiguous member list with register reductions
 //      over a few cooperating threads: SRD axis and MBS factor (Eqs. 2, 5-7) with
 //      phantom particles in wall cells, or the AT+a angular velocity from the moments
 //      about the cell's centre of mass,
-//   4. applies the collision to every particle, predicts the cell of step n+1 from the
-//      streamed position and the new velocity, counting-sorts by destination brick
-//      (warp-aggregated), reserves space in each destination with one global atomic
-//      per (CTA, destination), and writes the particles out coalesced.
+//   4. applies the collision to every particle, streams it for step n+1 (its only
+//      streaming per step), finds the brick of its next collision cell, ranks it within
+//      its destination group (warp-aggregated shared atomics), reserves space in each
+//      destination with one global atomic per (CTA, destination), and writes the
+//      particles out in contiguous runs.
 // HBM traffic per particle-step is one read and one write of the 28-byte particle:
 // no global per-cell arrays, no second sweep, no separate reorder pass (the permanent
 // reorder of Sec. III.B.3 happens in every step as part of the write).
@@ -42,7 +44,7 @@ struct CellParams<1> {  // AT+a: <w> = v_cm - <v_ran> (3), omega (3), rho_cm (3)
 };
 
 struct Layout {
-  size_t x, y, z, vx, vy, vz, id, gcell, ux, uy, uz, lcr, aux, perm, count, cstart, params, total;
+  size_t x, y, z, vx, vy, vz, id, gcell, ux, uy, uz, tag, perm, count, cstart, params, total;
 };
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
@@ -62,8 +64,7 @@ __host__ __device__ inline Layout make_layout(int cap, int bc, int nparams, bool
   L.ux = o; o += vran ? a4 : 0;
   L.uy = o; o += vran ? a4 : 0;
   L.uz = o; o += vran ? a4 : 0;
-  L.lcr = o; o += a4;
-  L.aux = o; o += a4;
+  L.tag = o; o += a4;
   L.perm = o; o += align16(size_t(cap) * 2);
   L.count = o; o += align16(size_t(bc) * 4);
   L.cstart = o; o += align16(size_t(bc + 1) * 4);
@@ -161,8 +162,9 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
   float* sux = reinterpret_cast<float*>(smem + lay.ux);  // AT+a: v_ran
   float* suy = reinterpret_cast<float*>(smem + lay.uy);
   float* suz = reinterpret_cast<float*>(smem + lay.uz);
-  uint32_t* slcr = reinterpret_cast<uint32_t*>(smem + lay.lcr);  // local cell | rank << 16
-  uint32_t* saux = reinterpret_cast<uint32_t*>(smem + lay.aux);  // dest code | rank << 5
+  // per particle: local cell | rank in cell << 16 (phases 2-4), then destination code |
+  // rank in destination group << 5 (phases 4-6)
+  uint32_t* stag = reinterpret_cast<uint32_t*>(smem + lay.tag);
   uint16_t* sperm = reinterpret_cast<uint16_t*>(smem + lay.perm);
   uint32_t* scount = reinterpret_cast<uint32_t*>(smem + lay.count);
   uint32_t* scstart = reinterpret_cast<uint32_t*>(smem + lay.cstart);
@@ -170,7 +172,7 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
 
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t s_cnt, s_halt;
-  __shared__ uint32_t gcount[28], gstart[29], gbase[28], gdest[28];
+  __shared__ uint32_t gcount[28], gbase[28], gdest[28];
   __shared__ uint32_t sh0[3], sh1[3];
   __shared__ float s_obs[kThreads / 32][13];
 
@@ -179,11 +181,6 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
   const int b = blockIdx.x;
   const int bc = g.brick_cells;
 
-  if (tid == 0) {
-    s_halt = *(volatile int32_t*)&a.ctrl->halted;
-  }
-  __syncthreads();
-  if (s_halt) return;
   const int64_t step64 = *(volatile int64_t*)&a.ctrl->step;
   const uint32_t step = (uint32_t)step64;
   const int par = (int)(step64 & 1);
@@ -192,13 +189,30 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
   uint32_t* cnt_src = a.cnt[par];
   uint32_t* cnt_dst = a.cnt[par ^ 1];
 
-  // ---- 1. load the brick ----
+  // ---- 1. load the brick (thread 0 starts the bulk copies at once) ----
   if (tid == 0) {
-    uint32_t c = cnt_src[b];
-    if (c > (uint32_t)g.cap) c = g.cap;
+    const uint32_t halted = *(volatile int32_t*)&a.ctrl->halted;
+    s_halt = halted;
+    uint32_t c = 0;
+    if (!halted) {
+      c = cnt_src[b];
+      if (c > (uint32_t)g.cap) c = g.cap;
+      cnt_src[b] = 0;  // this buffer becomes the destination of the next step
+      mbar_init(&bar, 1);
+      const uint32_t bytes = (uint32_t)(((c + 3) & ~3u) * 4);
+      mbar_expect_tx(&bar, 7u * bytes);
+      if (bytes) {
+        const size_t off = (size_t)b * g.cap;
+        bulk_g2s(sx, src.x[0] + off, bytes, &bar);
+        bulk_g2s(sy, src.x[1] + off, bytes, &bar);
+        bulk_g2s(sz, src.x[2] + off, bytes, &bar);
+        bulk_g2s(svx, src.v[0] + off, bytes, &bar);
+        bulk_g2s(svy, src.v[1] + off, bytes, &bar);
+        bulk_g2s(svz, src.v[2] + off, bytes, &bar);
+        bulk_g2s(sid, src.id + off, bytes, &bar);
+      }
+    }
     s_cnt = c;
-    cnt_src[b] = 0;  // this buffer becomes the destination of the next step
-    mbar_init(&bar, 1);
   }
   if (tid < 28) gcount[tid] = 0;
   if (tid == 32) {
@@ -209,21 +223,8 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
   }
   for (int c = tid; c < bc; c += kThreads) scount[c] = 0;
   __syncthreads();
+  if (s_halt) return;
   const int cnt = (int)s_cnt;
-  if (tid == 0) {
-    const uint32_t bytes = (uint32_t)(((cnt + 3) & ~3) * 4);
-    mbar_expect_tx(&bar, 7u * bytes);
-    if (bytes) {
-      const size_t off = (size_t)b * g.cap;
-      bulk_g2s(sx, src.x[0] + off, bytes, &bar);
-      bulk_g2s(sy, src.x[1] + off, bytes, &bar);
-      bulk_g2s(sz, src.x[2] + off, bytes, &bar);
-      bulk_g2s(svx, src.v[0] + off, bytes, &bar);
-      bulk_g2s(svy, src.v[1] + off, bytes, &bar);
-      bulk_g2s(svz, src.v[2] + off, bytes, &bar);
-      bulk_g2s(sid, src.id + off, bytes, &bar);
-    }
-  }
   if (!mbar_wait(&bar, 0)) {
     if (tid == 0) atomicOr(&a.ctrl->errors, kErrTimeout);
     mbar_wait(&bar, 0);  // give copies in flight one more bounded chance before leaving
@@ -236,11 +237,15 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
   const int ox = bx << g.Bs[0], oy = by << g.Bs[1], oz = bz << g.Bs[2];
   const uint32_t S0x = sh0[0], S0y = sh0[1], S0z = sh0[2];
 
-  // ---- 2. stream and rank each particle within its cell ----
+  // ---- 2. rank each particle within its collision cell ----
+  // Stored positions are already streamed for this step (the previous step streamed
+  // them when it predicted their brick); the stored velocity is the one they streamed
+  // with, before the kick.
   for (int i = tid; i < cnt; i += kThreads) {
-    uint32_t x = sx[i], y = sy[i], z = sz[i];
+    const uint32_t zraw = sz[i];
+    const uint32_t x = sx[i], y = sy[i], z = zraw & ~kCrossedBit;
     float vx = svx[i], vy = svy[i], vz = svz[i];
-    stream(g, x, y, z, vx, vy, vz);
+    collision_velocity(g, zraw, vx, vy, vz);
     const int cx = cell_axis(g, x, S0x, 0), cy = cell_axis(g, y, S0y, 1),
               cz = cell_axis(g, z, S0z, 2);
     const int lx = cx - ox, ly = cy - oy, lz = cz - oz;
@@ -253,8 +258,7 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
       lcr = 0xFFFFu;  // not binned here: keep the particle, skip its collision
       atomicOr(&a.ctrl->errors, kErrBinning);
     }
-    slcr[i] = lcr;
-    sx[i] = x; sy[i] = y; sz[i] = z;
+    stag[i] = lcr;
     if (g.debug) sgc[i] = (uint32_t)cx + (uint32_t)g.Lc[0] * ((uint32_t)cy + (uint32_t)g.Lc[1] * (uint32_t)cz);
     if constexpr (VAR == 1) {
       // AT+a: keep v_ran and w = v - v_ran
@@ -292,7 +296,7 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
   }
   __syncthreads();
   for (int i = tid; i < cnt; i += kThreads) {
-    const uint32_t lcr = slcr[i];
+    const uint32_t lcr = stag[i];
     const uint32_t lc = lcr & 0xFFFFu;
     if (lc != 0xFFFFu) sperm[scstart[lc] + (lcr >> 16)] = (uint16_t)i;
   }
@@ -385,7 +389,8 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
         float r0 = 0.f, r1 = 0.f, r2 = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f;
         for (int k = sub; k < n; k += tpc) {
           const int i = sperm[base + k];
-          r0 += rho_axis(g, sx[i], S0x); r1 += rho_axis(g, sy[i], S0y); r2 += rho_axis(g, sz[i], S0z);
+          r0 += rho_axis(g, sx[i], S0x); r1 += rho_axis(g, sy[i], S0y);
+          r2 += rho_axis(g, sz[i] & ~kCrossedBit, S0z);
           w0 += svx[i]; w1 += svy[i]; w2 += svz[i];
         }
         r0 = group_sum(r0, tpc); r1 = group_sum(r1, tpc); r2 = group_sum(r2, tpc);
@@ -399,7 +404,7 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
         for (int k = sub; k < n; k += tpc) {
           const int i = sperm[base + k];
           const float rx = rho_axis(g, sx[i], S0x) - rcx, ry = rho_axis(g, sy[i], S0y) - rcy,
-                      rz = rho_axis(g, sz[i], S0z) - rcz;
+                      rz = rho_axis(g, sz[i] & ~kCrossedBit, S0z) - rcz;
           const float wx = svx[i] - wmx, wy = svy[i] - wmy, wz = svz[i] - wmz;
           Mxx += rx * rx; Myy += ry * ry; Mzz += rz * rz;
           Mxy += rx * ry; Myz += ry * rz; Mzx += rz * rx;
@@ -445,15 +450,15 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
   }
   __syncthreads();
 
-  // ---- 4. collide, predict the next cell, count by destination brick ----
+  // ---- 4. collide, stream for step n+1, count by destination brick ----
   float o_px = 0, o_py = 0, o_pz = 0, o_e = 0, o_kxy = 0, o_kyz = 0, o_kzx = 0;
   float o_c[6] = {0, 0, 0, 0, 0, 0};
   const uint32_t S1x = sh1[0], S1y = sh1[1], S1z = sh1[2];
   const bool zper = !g.walls;
   for (int i = tid; i < cnt; i += kThreads) {
-    const uint32_t x = sx[i], y = sy[i], z = sz[i];
+    uint32_t x = sx[i], y = sy[i], z = sz[i] & ~kCrossedBit;
     float vbx = svx[i], vby = svy[i], vbz = svz[i];  // AT+a: w
-    const uint32_t lc = slcr[i] & 0xFFFFu;
+    const uint32_t lc = stag[i] & 0xFFFFu;
     float nx, ny, nz;
     if constexpr (VAR == 0) {
       nx = vbx; ny = vby; nz = vbz;
@@ -491,21 +496,23 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
       o_c[0] += dx * ry; o_c[1] += dy * rx; o_c[2] += dy * rz;
       o_c[3] += dz * ry; o_c[4] += dz * rx; o_c[5] += dx * rz;
     }
+    // stream for step n+1 (this is the only streaming of the particle per step) and
+    // find the brick of its next collision cell
+    stream(g, x, y, z, nx, ny, nz);
+    sx[i] = x; sy[i] = y; sz[i] = z;
     svx[i] = nx; svy[i] = ny; svz[i] = nz;
-    // the brick this particle occupies in step n+1
-    uint32_t x2 = x, y2 = y, z2 = z;
-    float ux2 = nx, uy2 = ny, uz2 = nz;
-    stream(g, x2, y2, z2, ux2, uy2, uz2);
-    const int qx = cell_axis(g, x2, S1x, 0) >> g.Bs[0];
-    const int qy = cell_axis(g, y2, S1y, 1) >> g.Bs[1];
-    const int qz = cell_axis(g, z2, S1z, 2) >> g.Bs[2];
+    const uint32_t zs = z & ~kCrossedBit;
+    const int qx = cell_axis(g, x, S1x, 0) >> g.Bs[0];
+    const int qy = cell_axis(g, y, S1y, 1) >> g.Bs[1];
+    const int qz = cell_axis(g, zs, S1z, 2) >> g.Bs[2];
     const int dxb = brick_step(qx, bx, g.nb[0], true);
     const int dyb = brick_step(qy, by, g.nb[1], true);
     const int dzb = brick_step(qz, bz, g.nb[2], zper);
     const uint32_t code = (dxb == 9 || dyb == 9 || dzb == 9)
                               ? 27u
                               : (uint32_t)((dxb + 1) + 3 * (dyb + 1) + 9 * (dzb + 1));
-    // warp-aggregated rank within the destination group
+    // warp-aggregated rank within the destination group: lanes of a warp with the same
+    // destination get consecutive slots, so the writes below are contiguous runs
     const uint32_t active = __activemask();
     const uint32_t peers = __match_any_sync(active, code);
     const int first = __ffs(peers) - 1;
@@ -513,7 +520,7 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
     if (lane == first) rank0 = atomicAdd(&gcount[code], (uint32_t)__popc(peers));
     rank0 = __shfl_sync(peers, rank0, first);
     const uint32_t rank = rank0 + (uint32_t)__popc(peers & ((1u << lane) - 1u));
-    saux[i] = code | (rank << 5);
+    stag[i] = code | (rank << 5);
   }
   if (g.obs) {
     const int w = tid >> 5;
@@ -527,11 +534,6 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
   __syncthreads();
 
   // ---- 5. reserve space in the destination bricks ----
-  if (tid == 0) {
-    uint32_t acc = 0;
-    for (int c = 0; c < 28; ++c) { gstart[c] = acc; acc += gcount[c]; }
-    gstart[28] = acc;
-  }
   if (tid < 27 && gcount[tid] > 0) {
     const int dxb = tid % 3 - 1, dyb = (tid / 3) % 3 - 1, dzb = tid / 9 - 1;
     int qx = bx + dxb, qy = by + dyb, qz = bz + dzb;
@@ -542,33 +544,26 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
     gdest[tid] = d;
     gbase[tid] = atomicAdd(&cnt_dst[d], gcount[tid]);
   }
-  if (g.obs && tid < 13) {
+  if (g.obs && tid >= 32 && tid < 32 + 13) {
+    const int q = tid - 32;
     double s = 0.0;
-    for (int w = 0; w < kThreads / 32; ++w) s += (double)s_obs[w][tid];
-    atomicAdd(&a.obs_partials[(b % kObsSlots) * kObsWidth + tid], s);
-  }
-  __syncthreads();
-  for (int i = tid; i < cnt; i += kThreads) {
-    const uint32_t au = saux[i];
-    sperm[gstart[au & 31u] + (au >> 5)] = (uint16_t)i;
+    for (int w = 0; w < kThreads / 32; ++w) s += (double)s_obs[w][q];
+    atomicAdd(&a.obs_partials[(b % kObsSlots) * kObsWidth + q], s);
   }
   __syncthreads();
 
-  // ---- 6. write out, grouped by destination (coalesced within each group) ----
-  for (int t = tid; t < cnt; t += kThreads) {
-    const int i = sperm[t];
-    const uint32_t code = saux[i] & 31u;
+  // ---- 6. write out: each particle to its reserved slot ----
+  for (int i = tid; i < cnt; i += kThreads) {
+    const uint32_t t = stag[i];
+    const uint32_t code = t & 31u;
     uint32_t d, slot;
     if (code < 27) {
       d = gdest[code];
-      slot = gbase[code] + (uint32_t)t - gstart[code];
+      slot = gbase[code] + (t >> 5);
     } else {
-      uint32_t x2 = sx[i], y2 = sy[i], z2 = sz[i];
-      float ux = svx[i], uy = svy[i], uz = svz[i];
-      stream(g, x2, y2, z2, ux, uy, uz);
-      const int qx = cell_axis(g, x2, S1x, 0) >> g.Bs[0];
-      const int qy = cell_axis(g, y2, S1y, 1) >> g.Bs[1];
-      const int qz = cell_axis(g, z2, S1z, 2) >> g.Bs[2];
+      const int qx = cell_axis(g, sx[i], S1x, 0) >> g.Bs[0];
+      const int qy = cell_axis(g, sy[i], S1y, 1) >> g.Bs[1];
+      const int qz = cell_axis(g, sz[i] & ~kCrossedBit, S1z, 2) >> g.Bs[2];
       d = (uint32_t)(qx + g.nb[0] * (qy + g.nb[1] * qz));
       slot = atomicAdd(&cnt_dst[d], 1u);
     }
