@@ -129,9 +129,9 @@ void finish_bricks(Geom& g) {
   g.tpc = tpc;
 }
 
-// cells per brick: powers of two, grown on the shortest axis first, ~1280 particles
+// cells per brick: powers of two, grown on the shortest axis first, ~kBrickParticles
 void choose_bricks(Geom& g, double n_c) {
-  const int target = std::max(1, (int)std::lround(1280.0 / std::max(n_c, 1e-3)));
+  const int target = std::max(1, (int)std::lround(kBrickParticles / std::max(n_c, 1e-3)));
   int B[3] = {1, 1, 1};
   for (;;) {
     int best = -1;

@@ -67,7 +67,8 @@ struct Spill {
   uint32_t capacity;
 };
 
-constexpr int kStepThreads = 256;  // threads per CTA of the fused step kernel
+constexpr int kStepThreads = 128;  // threads per CTA of the fused step kernel
+constexpr int kBrickParticles = 640;  // target mean particles per brick
 constexpr int kObsSlots = 128;   // partial-sum slots per step (spreads FP64 atomics)
 constexpr int kObsWidth = 16;    // doubles per observables row
 

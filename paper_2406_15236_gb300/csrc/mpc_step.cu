@@ -172,8 +172,8 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
 
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t s_cnt, s_halt;
+  __shared__ int64_t s_step;
   __shared__ uint32_t gcount[28], gbase[28], gdest[28];
-  __shared__ uint32_t sh0[3], sh1[3];
   __shared__ float s_obs[kThreads / 32][13];
 
   const int tid = threadIdx.x;
@@ -181,50 +181,57 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
   const int b = blockIdx.x;
   const int bc = g.brick_cells;
 
-  const int64_t step64 = *(volatile int64_t*)&a.ctrl->step;
-  const uint32_t step = (uint32_t)step64;
-  const int par = (int)(step64 & 1);
-  const PBuf& src = a.buf[par];
-  const PBuf& dst = a.buf[par ^ 1];
-  uint32_t* cnt_src = a.cnt[par];
-  uint32_t* cnt_dst = a.cnt[par ^ 1];
-
-  // ---- 1. load the brick (thread 0 starts the bulk copies at once) ----
+  // ---- 1. load the brick: thread 0 reads the step, the halt flag and both count slots
+  // in one round trip, then starts the bulk copies ----
   if (tid == 0) {
-    const uint32_t halted = *(volatile int32_t*)&a.ctrl->halted;
+    const int64_t st = *(volatile int64_t*)&a.ctrl->step;
+    const int32_t halted = *(volatile int32_t*)&a.ctrl->halted;
+    const uint32_t c_even = a.cnt[0][b], c_odd = a.cnt[1][b];
+    s_step = st;
     s_halt = halted;
     uint32_t c = 0;
     if (!halted) {
-      c = cnt_src[b];
+      const int p = (int)(st & 1);
+      c = p ? c_odd : c_even;
       if (c > (uint32_t)g.cap) c = g.cap;
-      cnt_src[b] = 0;  // this buffer becomes the destination of the next step
+      a.cnt[p][b] = 0;  // this buffer becomes the destination of the next step
       mbar_init(&bar, 1);
       const uint32_t bytes = (uint32_t)(((c + 3) & ~3u) * 4);
       mbar_expect_tx(&bar, 7u * bytes);
       if (bytes) {
+        const PBuf& sb = a.buf[p];
         const size_t off = (size_t)b * g.cap;
-        bulk_g2s(sx, src.x[0] + off, bytes, &bar);
-        bulk_g2s(sy, src.x[1] + off, bytes, &bar);
-        bulk_g2s(sz, src.x[2] + off, bytes, &bar);
-        bulk_g2s(svx, src.v[0] + off, bytes, &bar);
-        bulk_g2s(svy, src.v[1] + off, bytes, &bar);
-        bulk_g2s(svz, src.v[2] + off, bytes, &bar);
-        bulk_g2s(sid, src.id + off, bytes, &bar);
+        bulk_g2s(sx, sb.x[0] + off, bytes, &bar);
+        bulk_g2s(sy, sb.x[1] + off, bytes, &bar);
+        bulk_g2s(sz, sb.x[2] + off, bytes, &bar);
+        bulk_g2s(svx, sb.v[0] + off, bytes, &bar);
+        bulk_g2s(svy, sb.v[1] + off, bytes, &bar);
+        bulk_g2s(svz, sb.v[2] + off, bytes, &bar);
+        bulk_g2s(sid, sb.id + off, bytes, &bar);
       }
     }
     s_cnt = c;
   }
   if (tid < 28) gcount[tid] = 0;
-  if (tid == 32) {
-    const uint3 s0 = lattice_shift(g, step);
-    const uint3 s1 = lattice_shift(g, step + 1);
-    sh0[0] = s0.x; sh0[1] = s0.y; sh0[2] = s0.z;
-    sh1[0] = s1.x; sh1[1] = s1.y; sh1[2] = s1.z;
-  }
   for (int c = tid; c < bc; c += kThreads) scount[c] = 0;
   __syncthreads();
   if (s_halt) return;
+  const int64_t step64 = s_step;
+  const uint32_t step = (uint32_t)step64;
+  const int par = (int)(step64 & 1);
+  const PBuf& dst = a.buf[par ^ 1];
+  uint32_t* cnt_dst = a.cnt[par ^ 1];
   const int cnt = (int)s_cnt;
+  // lattice shifts of this step and the next: one lane per warp draws, the warp shares
+  uint3 s0 = make_uint3(0, 0, 0), s1 = make_uint3(0, 0, 0);
+  if (lane == 0) {
+    s0 = lattice_shift(g, step);
+    s1 = lattice_shift(g, step + 1);
+  }
+  const uint32_t S0x = __shfl_sync(0xffffffffu, s0.x, 0), S0y = __shfl_sync(0xffffffffu, s0.y, 0),
+                 S0z = __shfl_sync(0xffffffffu, s0.z, 0);
+  const uint32_t S1x = __shfl_sync(0xffffffffu, s1.x, 0), S1y = __shfl_sync(0xffffffffu, s1.y, 0),
+                 S1z = __shfl_sync(0xffffffffu, s1.z, 0);
   if (!mbar_wait(&bar, 0)) {
     if (tid == 0) atomicOr(&a.ctrl->errors, kErrTimeout);
     mbar_wait(&bar, 0);  // give copies in flight one more bounded chance before leaving
@@ -235,7 +242,6 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
   const int by = (b / g.nb[0]) % g.nb[1];
   const int bz = b / (g.nb[0] * g.nb[1]);
   const int ox = bx << g.Bs[0], oy = by << g.Bs[1], oz = bz << g.Bs[2];
-  const uint32_t S0x = sh0[0], S0y = sh0[1], S0z = sh0[2];
 
   // ---- 2. rank each particle within its collision cell ----
   // Stored positions are already streamed for this step (the previous step streamed
@@ -453,7 +459,6 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
   // ---- 4. collide, stream for step n+1, count by destination brick ----
   float o_px = 0, o_py = 0, o_pz = 0, o_e = 0, o_kxy = 0, o_kyz = 0, o_kzx = 0;
   float o_c[6] = {0, 0, 0, 0, 0, 0};
-  const uint32_t S1x = sh1[0], S1y = sh1[1], S1z = sh1[2];
   const bool zper = !g.walls;
   for (int i = tid; i < cnt; i += kThreads) {
     uint32_t x = sx[i], y = sy[i], z = sz[i] & ~kCrossedBit;
