@@ -341,10 +341,15 @@ static double min_eigenvalue_sym3(const double A[3][3]) {
   return q + 2.0 * pp * cos(phi + 2.0 * M_PI / 3.0);
 }
 
-/* rounding-sensitivity of omega x r_ic for a float32 evaluation: |r_i| sum_j |r_j||w_j|
- * divided by the smallest eigenvalue of J on the space it inverts (test diagnostics) */
+/* First-order sensitivity of the new velocities to float32 rounding in the cell's
+ * angular-momentum solve (test diagnostics, in units of the rounding unit u): relative
+ * rounding of every product and of the centre-of-mass positions (|rho| <= 1) perturbs
+ * L = sum r_j x w_j by ~ sum |r_j||w_j| + sum |w_j| and J by ~ 2 sum |r_j|; omega = J^-1 L
+ * then moves by 1/lambda_min times (dL + |omega| dJ), and omega x r_i by that times |r_i|,
+ * plus |omega| times the rounding of r_i itself.  Returns the factor multiplying |r_i|
+ * (per cell); the caller adds the direct 2|omega| term. */
 static double omega_sensitivity(int64_t n, const double J[3][3], const double pair_axis[3],
-                                double sum_rw) {
+                                double sum_rw, double sum_w, double sum_r, double omega_norm) {
   if (n <= 1) return 0.0;
   double lam;
   if (n == 2) {
@@ -354,7 +359,7 @@ static double omega_sensitivity(int64_t n, const double J[3][3], const double pa
   } else {
     lam = min_eigenvalue_sym3(J);
   }
-  return lam > 0.0 ? sum_rw / lam : INFINITY;
+  return lam > 0.0 ? (sum_rw + sum_w + 2.0 * omega_norm * sum_r) / lam : INFINITY;
 }
 
 /* omega = J^{-1} Lr for the geometric moment-of-inertia tensor J of a cell
@@ -561,7 +566,7 @@ int orc_step(const orc_params* p, int64_t N, uint32_t* X, double* V, const uint3
       double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
       double Lr[3] = {0, 0, 0};
       double pair_axis[3] = {0, 0, 0};
-      double sum_rw = 0.0;
+      double sum_rw = 0.0, sum_w = 0.0, sum_r = 0.0;
       if (n == 2)
         for (int a = 0; a < 3; ++a) pair_axis[a] = rho[3 * mem[0] + a] - rho[3 * mem[1] + a];
 
@@ -594,11 +599,15 @@ int orc_step(const orc_params* p, int64_t N, uint32_t* X, double* V, const uint3
             for (int b = 0; b < 3; ++b) J[a][b] += (a == b ? r2 : 0.0) - r[a] * r[b];
           cross3(r, w, rxw);
           for (int a = 0; a < 3; ++a) Lr[a] += rxw[a];
-          sum_rw += sqrt(r2) * sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+          double wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+          sum_rw += sqrt(r2) * wn;
+          sum_w += wn;
+          sum_r += sqrt(r2);
         }
         double omega[3];
         flags |= solve_inertia(n, J, Lr, pair_axis, omega);
-        double sens = sens_out ? omega_sensitivity(n, J, pair_axis, sum_rw) : 0.0;
+        double on = sqrt(omega[0] * omega[0] + omega[1] * omega[1] + omega[2] * omega[2]);
+        double sens = sens_out ? omega_sensitivity(n, J, pair_axis, sum_rw, sum_w, sum_r, on) : 0.0;
         for (int64_t k = 0; k < n; ++k) {
           int64_t i = mem[k];
           double r[3], wxr[3];
@@ -606,7 +615,8 @@ int orc_step(const orc_params* p, int64_t N, uint32_t* X, double* V, const uint3
           cross3(omega, r, wxr);
           for (int a = 0; a < 3; ++a)
             vnew[3 * i + a] = vcm[a] + vran[3 * k + a] - vrm[a] + wxr[a];
-          if (sens_out) sens_out[i] = sens * sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+          if (sens_out)
+            sens_out[i] = sens * sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]) + 2.0 * on;
         }
         free(vran);
       } else {
@@ -630,18 +640,23 @@ int orc_step(const orc_params* p, int64_t N, uint32_t* X, double* V, const uint3
             for (int b = 0; b < 3; ++b) J[a][b] += (a == b ? r2 : 0.0) - r[a] * r[b];
           cross3(r, w, rxw);
           for (int a = 0; a < 3; ++a) Lr[a] += rxw[a];
-          sum_rw += sqrt(r2) * sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+          double wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+          sum_rw += sqrt(r2) * wn;
+          sum_w += wn;
+          sum_r += sqrt(r2);
         }
         double omega[3];
         flags |= solve_inertia(n, J, Lr, pair_axis, omega);
-        double sens = sens_out ? omega_sensitivity(n, J, pair_axis, sum_rw) : 0.0;
+        double on = sqrt(omega[0] * omega[0] + omega[1] * omega[1] + omega[2] * omega[2]);
+        double sens = sens_out ? omega_sensitivity(n, J, pair_axis, sum_rw, sum_w, sum_r, on) : 0.0;
         for (int64_t k = 0; k < n; ++k) {
           int64_t i = mem[k];
           double r[3], wxr[3];
           for (int a = 0; a < 3; ++a) r[a] = rho[3 * i + a] - rcm[a];
           cross3(omega, r, wxr);
           for (int a = 0; a < 3; ++a) vnew[3 * i + a] = vcm[a] + dv[3 * k + a] + wxr[a];
-          if (sens_out) sens_out[i] = sens * sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+          if (sens_out)
+            sens_out[i] = sens * sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]) + 2.0 * on;
         }
         free(dv);
       }

@@ -132,16 +132,13 @@ __device__ __forceinline__ float group_sum(float v, int tpc) {
 }
 
 // brick-axis offset of a neighbour: 0 same, +-1 adjacent (with periodic wrap), 9 other
-__device__ __forceinline__ int brick_step(int q, int b, int nb, bool periodic) {
-  if (q == b) return 0;
-  int up = b + 1, dn = b - 1;
+__device__ __forceinline__ int brick_delta(int q, int b, int nb, bool periodic) {
+  int d = q - b;
   if (periodic) {
-    if (up == nb) up = 0;
-    if (dn < 0) dn = nb - 1;
+    if (d > 1) d -= nb;
+    else if (d < -1) d += nb;
   }
-  if (q == up) return 1;
-  if (q == dn) return -1;
-  return 9;
+  return (d >= -1 && d <= 1) ? d : 9;
 }
 
 // --- the step kernel ---------------------------------------------------------------
@@ -510,9 +507,9 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
     const int qx = cell_axis(g, x, S1x, 0) >> g.Bs[0];
     const int qy = cell_axis(g, y, S1y, 1) >> g.Bs[1];
     const int qz = cell_axis(g, zs, S1z, 2) >> g.Bs[2];
-    const int dxb = brick_step(qx, bx, g.nb[0], true);
-    const int dyb = brick_step(qy, by, g.nb[1], true);
-    const int dzb = brick_step(qz, bz, g.nb[2], zper);
+    const int dxb = brick_delta(qx, bx, g.nb[0], true);
+    const int dyb = brick_delta(qy, by, g.nb[1], true);
+    const int dzb = brick_delta(qz, bz, g.nb[2], zper);
     const uint32_t code = (dxb == 9 || dyb == 9 || dzb == 9)
                               ? 27u
                               : (uint32_t)((dxb + 1) + 3 * (dyb + 1) + 9 * (dzb + 1));

@@ -2,10 +2,12 @@
 
 Velocity error of a particle: |v_gpu - v_ref| / max(|v_ref|, sqrt(kT/m)), bar 1e-5.
 For the angular-momentum variants the float32 kernel solves J omega = L per cell, and
-float32 rounding of the cell sums (relative u = 2^-24 per term) reaches the velocity
-amplified by sens_i = |r_i| sum_j |r_j||w_j| / lambda_min(J) (exported by the oracle);
-the bar of a particle is max(1e-5, 16 u sens_i / scale_i) (the measured ratio of error
-to u sens_i stays below 3).  It widens only for near-collinear cells of 2-5 particles.
+float32 rounding (relative u = 2^-24 per operation) of the products and of the
+centre-of-mass positions reaches the velocity amplified by the first-order factor sens_i
+the oracle exports (1/lambda_min(J) times the perturbations of L and J, times |r_i|,
+plus the rounding of r_i times |omega|); the bar of a particle is
+max(1e-5, 16 u sens_i / scale_i).  It widens only for near-collinear cells and
+near-coincident pairs of 2-5 particles.
 Integer results (positions, collision cells, per-cell counts) must agree bit-exactly.
 """
 import numpy as np
