@@ -53,6 +53,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-observables", action="store_true",
+                    help="do not accumulate observables inside the step (they are then "
+                         "reduced from the state when read)")
     return ap.parse_args(argv)
 
 
@@ -64,6 +67,7 @@ def workload(args) -> dict:
             "L": args.L, "n_c": args.n_c, "variant": args.variant, "h": args.h, "kT": 1.0,
             "particles_per_box": N, "seed": args.seed,
             "l2": "inputs larger than L2 (28 B/particle state in HBM), no flush needed",
+            "observables_per_step": not args.no_observables,
             "parallelism": "replicas"}
 
 
@@ -276,7 +280,8 @@ def run_ours(args):
 
     variant = mpc.MPC_AT_A if args.variant == "at_a" else mpc.MPC_SRD
     kw = dict(L=args.L, n_c=args.n_c, h=args.h, alpha_deg=130.0, kT=1.0, variant=variant,
-              seed=args.seed + rank, box_id=rank, flags=mpc.MPC_FLAG_OBSERVABLES)
+              seed=args.seed + rank, box_id=rank,
+              flags=0 if args.no_observables else mpc.MPC_FLAG_OBSERVABLES)
     sim = mpc.Simulation(**kw)
     N = sim.N
     stream = torch.cuda.current_stream()

@@ -462,6 +462,8 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
     float vbx = svx[i], vby = svy[i], vbz = svz[i];  // AT+a: w
     const uint32_t lc = stag[i] & 0xFFFFu;
     float nx, ny, nz;
+    // positions relative to the collision-cell centre (collisional stress, AT+a omega x r)
+    const float px = rho_axis(g, x, S0x), py = rho_axis(g, y, S0y), pz = rho_axis(g, z, S0z);
     if constexpr (VAR == 0) {
       nx = vbx; ny = vby; nz = vbz;
       if (lc != 0xFFFFu) {
@@ -481,8 +483,7 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
       nx = vbx; ny = vby; nz = vbz;
       if (lc != 0xFFFFu) {
         const float* P = spar + lc;
-        const float rx = rho_axis(g, x, S0x) - P[6 * bc], ry = rho_axis(g, y, S0y) - P[7 * bc],
-                    rz = rho_axis(g, z, S0z) - P[8 * bc];
+        const float rx = px - P[6 * bc], ry = py - P[7 * bc], rz = pz - P[8 * bc];
         const float wx = P[3 * bc], wy = P[4 * bc], wz = P[5 * bc];
         nx = P[0] + ux + (wy * rz - wz * ry);
         ny = P[bc] + uy + (wz * rx - wx * rz);
@@ -493,10 +494,9 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
       o_px += nx; o_py += ny; o_pz += nz;
       o_e += nx * nx + ny * ny + nz * nz;
       o_kxy += vbx * vby; o_kyz += vby * vbz; o_kzx += vbz * vbx;
-      const float rx = rho_axis(g, x, S0x), ry = rho_axis(g, y, S0y), rz = rho_axis(g, z, S0z);
       const float dx = nx - vbx, dy = ny - vby, dz = nz - vbz;
-      o_c[0] += dx * ry; o_c[1] += dy * rx; o_c[2] += dy * rz;
-      o_c[3] += dz * ry; o_c[4] += dz * rx; o_c[5] += dx * rz;
+      o_c[0] += dx * py; o_c[1] += dy * px; o_c[2] += dy * pz;
+      o_c[3] += dz * py; o_c[4] += dz * px; o_c[5] += dx * pz;
     }
     // stream for step n+1 (this is the only streaming of the particle per step) and
     // find the brick of its next collision cell
@@ -513,15 +513,21 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
     const uint32_t code = (dxb == 9 || dyb == 9 || dzb == 9)
                               ? 27u
                               : (uint32_t)((dxb + 1) + 3 * (dyb + 1) + 9 * (dzb + 1));
-    // warp-aggregated rank within the destination group: lanes of a warp with the same
-    // destination get consecutive slots, so the writes below are contiguous runs
+    // rank within the destination group: particles that stay in this brick (most of
+    // them) get consecutive slots through one warp ballot, so their writes below are
+    // contiguous runs; the others take a shared-memory atomic each
     const uint32_t active = __activemask();
-    const uint32_t peers = __match_any_sync(active, code);
-    const int first = __ffs(peers) - 1;
-    uint32_t rank0 = 0;
-    if (lane == first) rank0 = atomicAdd(&gcount[code], (uint32_t)__popc(peers));
-    rank0 = __shfl_sync(peers, rank0, first);
-    const uint32_t rank = rank0 + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+    const uint32_t stay = __ballot_sync(active, code == 13u);
+    uint32_t rank;
+    if (code == 13u) {
+      const int first = __ffs(stay) - 1;
+      uint32_t rank0 = 0;
+      if (lane == first) rank0 = atomicAdd(&gcount[13], (uint32_t)__popc(stay));
+      rank0 = __shfl_sync(stay, rank0, first);
+      rank = rank0 + (uint32_t)__popc(stay & ((1u << lane) - 1u));
+    } else {
+      rank = atomicAdd(&gcount[code], 1u);
+    }
     stag[i] = code | (rank << 5);
   }
   if (g.obs) {
