@@ -161,8 +161,8 @@ mpc_status validate(const mpc_params* p) {
   if (!(p->h > 0.0) || !std::isfinite(p->h)) return fail(nullptr, MPC_EINVAL, "h must be > 0");
   if (!(p->kT > 0.0) || !(p->m > 0.0)) return fail(nullptr, MPC_EINVAL, "kT and m must be > 0");
   if (!(p->n_c > 0.0)) return fail(nullptr, MPC_EINVAL, "n_c must be > 0");
-  if (p->variant != MPC_SRD && p->variant != MPC_AT_A)
-    return fail(nullptr, MPC_EINVAL, "variant not supported (SRD and AT+a are)");
+  if (p->variant != MPC_SRD && p->variant != MPC_AT_A && p->variant != MPC_SRD_A)
+    return fail(nullptr, MPC_EINVAL, "variant must be MPC_SRD, MPC_AT_A or MPC_SRD_A");
   if (p->thermostat && p->variant != MPC_SRD)
     return fail(nullptr, MPC_EINVAL, "the MBS thermostat applies to SRD only");
   if (p->walls_z && p->variant != MPC_SRD)

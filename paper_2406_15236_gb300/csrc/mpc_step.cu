@@ -42,6 +42,11 @@ struct CellParams<1> {  // AT+a: <w> = v_cm - <v_ran> (3), omega (3), rho_cm (3)
   static constexpr int kParams = 9;
   static constexpr bool kStoresRandomVelocity = true;
 };
+template <>
+struct CellParams<2> {  // SRD+a: v_cm (3), omega (3), rho_cm (3), rotation axis (3)
+  static constexpr int kParams = 12;
+  static constexpr bool kStoresRandomVelocity = false;
+};
 
 struct Layout {
   size_t x, y, z, vx, vy, vz, id, gcell, ux, uy, uz, tag, perm, count, cstart, params, total;
@@ -388,7 +393,8 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
           P[6 * bc] = kappa;
         }
       } else {
-        // AT+a: first pass -- centre of mass and mean w = v - v_ran
+        // angular-momentum-conserving variants.  First pass: centre of mass and mean of
+        // w (AT+a: w = v - v_ran; SRD+a: w = v, so the mean is v_cm)
         float r0 = 0.f, r1 = 0.f, r2 = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f;
         for (int k = sub; k < n; k += tpc) {
           const int i = sperm[base + k];
@@ -401,14 +407,34 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
         const float inv = 1.0f / fmaxf((float)n, 1.0f);
         const float rcx = r0 * inv, rcy = r1 * inv, rcz = r2 * inv;
         const float wmx = w0 * inv, wmy = w1 * inv, wmz = w2 * inv;
-        // second pass: moments and angular momentum of w about the centre of mass
+        // SRD+a: the cell's random rotation axis (every lane of the group draws it)
+        float ax = 0.f, ay = 0.f, az = 0.f;
+        if constexpr (VAR == 2) {
+          const uint4 r = draw(g, cg, step, kTagAxis, 0u);
+          az = 2.0f * u01(r.x) - 1.0f;
+          const float st = sqrtf(fmaxf(0.0f, 1.0f - az * az));
+          float sphi, cphi;
+          sincospif(2.0f * u01(r.y), &sphi, &cphi);
+          ax = st * cphi;
+          ay = st * sphi;
+        }
+        // second pass: moments about the centre of mass and the angular momentum the
+        // collision would change -- AT+a: of w - <w>; SRD+a (Eq. 4): of v_ic - D v_ic
         float Mxx = 0.f, Myy = 0.f, Mzz = 0.f, Mxy = 0.f, Myz = 0.f, Mzx = 0.f;
         float Lx = 0.f, Ly = 0.f, Lz = 0.f;
         for (int k = sub; k < n; k += tpc) {
           const int i = sperm[base + k];
           const float rx = rho_axis(g, sx[i], S0x) - rcx, ry = rho_axis(g, sy[i], S0y) - rcy,
                       rz = rho_axis(g, sz[i] & ~kCrossedBit, S0z) - rcz;
-          const float wx = svx[i] - wmx, wy = svy[i] - wmy, wz = svz[i] - wmz;
+          float wx = svx[i] - wmx, wy = svy[i] - wmy, wz = svz[i] - wmz;
+          if constexpr (VAR == 2) {
+            const float nr = ax * wx + ay * wy + az * wz;
+            const float t = (1.0f - g.cos_a) * nr;
+            const float dx = g.cos_a * wx + g.sin_a * (ay * wz - az * wy) + t * ax;
+            const float dy = g.cos_a * wy + g.sin_a * (az * wx - ax * wz) + t * ay;
+            const float dz = g.cos_a * wz + g.sin_a * (ax * wy - ay * wx) + t * az;
+            wx -= dx; wy -= dy; wz -= dz;
+          }
           Mxx += rx * rx; Myy += ry * ry; Mzz += rz * rz;
           Mxy += rx * ry; Myz += ry * rz; Mzx += rz * rx;
           Lx += ry * wz - rz * wy; Ly += rz * wx - rx * wz; Lz += rx * wy - ry * wx;
@@ -447,6 +473,9 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
           P[0 * bc] = wmx; P[1 * bc] = wmy; P[2 * bc] = wmz;
           P[3 * bc] = ox_; P[4 * bc] = oy_; P[5 * bc] = oz_;
           P[6 * bc] = rcx; P[7 * bc] = rcy; P[8 * bc] = rcz;
+          if constexpr (VAR == 2) {
+            P[9 * bc] = ax; P[10 * bc] = ay; P[11 * bc] = az;
+          }
         }
       }
     }
@@ -476,6 +505,22 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
         nx = vcx + kap * (g.cos_a * rx + g.sin_a * (ay * rz - az * ry) + t * ax);
         ny = vcy + kap * (g.cos_a * ry + g.sin_a * (az * rx - ax * rz) + t * ay);
         nz = vcz + kap * (g.cos_a * rz + g.sin_a * (ax * ry - ay * rx) + t * az);
+      }
+    } else if constexpr (VAR == 2) {
+      // SRD+a, Eq. (3): v' = v_cm + D v_ic + omega x r_ic
+      nx = vbx; ny = vby; nz = vbz;
+      if (lc != 0xFFFFu) {
+        const float* P = spar + lc;
+        const float vcx = P[0], vcy = P[bc], vcz = P[2 * bc];
+        const float wx = P[3 * bc], wy = P[4 * bc], wz = P[5 * bc];
+        const float rx = px - P[6 * bc], ry = py - P[7 * bc], rz = pz - P[8 * bc];
+        const float ax = P[9 * bc], ay = P[10 * bc], az = P[11 * bc];
+        const float ux = vbx - vcx, uy = vby - vcy, uz = vbz - vcz;
+        const float nr = ax * ux + ay * uy + az * uz;
+        const float t = (1.0f - g.cos_a) * nr;
+        nx = vcx + g.cos_a * ux + g.sin_a * (ay * uz - az * uy) + t * ax + (wy * rz - wz * ry);
+        ny = vcy + g.cos_a * uy + g.sin_a * (az * ux - ax * uz) + t * ay + (wz * rx - wx * rz);
+        nz = vcz + g.cos_a * uz + g.sin_a * (ax * uy - ay * ux) + t * az + (wx * ry - wy * rx);
       }
     } else {
       const float ux = sux[i], uy = suy[i], uz = suz[i];
@@ -626,7 +671,9 @@ __global__ void k_advance(const StepArgs a) {
 }
 
 size_t step_smem_bytes(const Geom& g) {
-  return g.variant == 0 ? layout_for<0>(g).total : layout_for<1>(g).total;
+  if (g.variant == 0) return layout_for<0>(g).total;
+  if (g.variant == 1) return layout_for<1>(g).total;
+  return layout_for<2>(g).total;
 }
 
 cudaError_t configure_step_kernels(const Geom& g) {
@@ -634,8 +681,10 @@ cudaError_t configure_step_kernels(const Geom& g) {
   cudaError_t e = cudaSuccess;
   if (g.variant == 0)
     e = cudaFuncSetAttribute(k_step<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  else
+  else if (g.variant == 1)
     e = cudaFuncSetAttribute(k_step<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  else
+    e = cudaFuncSetAttribute(k_step<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   return e;
 }
 
@@ -643,8 +692,10 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t s) {
   const size_t bytes = step_smem_bytes(a.g);
   if (a.g.variant == 0)
     k_step<0><<<a.g.nbricks, kThreads, bytes, s>>>(a);
-  else
+  else if (a.g.variant == 1)
     k_step<1><<<a.g.nbricks, kThreads, bytes, s>>>(a);
+  else
+    k_step<2><<<a.g.nbricks, kThreads, bytes, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -90,6 +90,14 @@ def test_at_a_per_step():
     assert over < 2e-3
 
 
+def test_srd_a_per_step():
+    """MPC-SRD+a, Eqs. (3)-(4): rotation plus the angular-momentum restoring term."""
+    kw = dict(L=16, n_c=10.0, h=0.1, alpha_deg=130.0, variant=2, seed=4)
+    log = []
+    _run_parity(kw, 12, strict_flags=oracle.FLAG_DEGENERATE, log=log)
+    assert max(e["over_tol"] for e in log) < 2e-3
+
+
 def test_srd_mbs_walls_gravity_per_step():
     kw = dict(L=16, n_c=10.0, h=0.1, alpha_deg=130.0, thermostat=1, walls_z=1,
               gravity=(0.02, 0.0, 0.0), seed=2)
@@ -99,7 +107,7 @@ def test_srd_mbs_walls_gravity_per_step():
     assert worst <= par.VEL_TOL
 
 
-@pytest.mark.parametrize("variant,h", [(0, 0.1), (1, 0.05)])
+@pytest.mark.parametrize("variant,h", [(0, 0.1), (1, 0.05), (2, 0.1)])
 def test_ragged_box(variant, h):
     kw = dict(L=(12, 10, 7), n_c=3.7, h=h, alpha_deg=90.0, variant=variant, seed=11)
     _run_parity(kw, 6, strict_flags=oracle.FLAG_DEGENERATE)

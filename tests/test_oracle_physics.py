@@ -58,12 +58,11 @@ def test_equipartition_and_maxwell_boltzmann_after_srd():
     assert np.abs(P).max() < 1e-9
 
 
-def test_poiseuille_flow_between_no_slip_walls():
-    """Body force g along x, bounce-back walls + phantom particles at z = 0, Lz, MBS
-    thermostat: steady profile v_x(z) = (rho g / 2 eta) z (Lz - z) (plus a small slip)."""
-    Lz, g, n_c = 10, 0.05, 10.0
+def poiseuille_eta(Lz=10, g=0.05, n_c=10.0, seed=5):
+    """The oracle's viscosity estimate from a Poiseuille profile: returns (eta, slip,
+    profile, z, mean temperature)."""
     p = oracle.params(L=(6, 6, Lz), n_c=n_c, h=0.1, alpha_deg=130, walls_z=1, thermostat=1,
-                      g=(g, 0, 0), seed=5)
+                      g=(g, 0, 0), seed=seed)
     X, V, ids = oracle.init(p)
     F = oracle.fixed_bits(p)
     nb = 2 * Lz
@@ -82,7 +81,14 @@ def test_poiseuille_flow_between_no_slip_walls():
     v = prof / cnt
     M = np.stack([z * (Lz - z), np.ones_like(z)], 1)
     (A, slip), *_ = np.linalg.lstsq(M, v, rcond=None)
-    eta = n_c * g / (2 * A)
+    return n_c * g / (2 * A), slip, v, z, float(np.mean(temps))
+
+
+def test_poiseuille_flow_between_no_slip_walls():
+    """Body force g along x, bounce-back walls + phantom particles at z = 0, Lz, MBS
+    thermostat: steady profile v_x(z) = (rho g / 2 eta) z (Lz - z) (plus a small slip)."""
+    Lz, g, n_c = 10, 0.05, 10.0
+    eta, slip, v, z, temp = poiseuille_eta(Lz, g, n_c)
     eta_th = eta_srd(n_c, 0.1, 130)
     assert abs(eta - eta_th) / eta_th < 0.05, eta
     vmax = n_c * g * Lz**2 / (8 * eta_th)
@@ -92,4 +98,4 @@ def test_poiseuille_flow_between_no_slip_walls():
     assert v.min() > 0
     # the thermostat removes the viscous heating (temperature about the flow profile
     # is reported by the kinetic estimator including the mean flow, so allow vmax^2/3)
-    assert abs(np.mean(temps) - 1.0) < 0.05 + vmax**2 / 3
+    assert abs(temp - 1.0) < 0.05 + vmax**2 / 3
