@@ -62,7 +62,16 @@ typedef enum {
 
 enum {
   MPC_FLAG_OBSERVABLES = 1u,  /* accumulate observables inside every step */
-  MPC_FLAG_DEBUG_CELLS = 2u   /* keep each particle's collision cell and per-cell counts */
+  MPC_FLAG_DEBUG_CELLS = 2u,  /* keep each particle's collision cell and per-cell counts */
+  /* Bit-reproducible trajectories (Sec. III.B, "Reproducibility"): every per-cell sum and
+   * every observable is accumulated in 64-bit fixed point (cell sums: 32 fraction bits;
+   * observables: 24), so results do not depend on the order of particles in memory,
+   * on the brick geometry, the threads per cell, or on which other boxes share a batch.
+   * Range: each summed per-particle term (a velocity component, a squared relative
+   * speed, a component of r x v) must stay below 2^15 in magnitude; a larger term makes
+   * the next synchronising call return MPC_ESTATE.  Sums of the observables must stay
+   * below 2^39 in magnitude. */
+  MPC_FLAG_DETERMINISTIC = 4u
 };
 
 typedef struct {
@@ -82,6 +91,12 @@ typedef struct {
   uint32_t flags;        /* MPC_FLAG_* */
   int32_t capacity;      /* particles per brick buffer; 0 = chosen from n_c */
   int32_t graph_steps;   /* steps per captured CUDA graph; 0 = default (16) */
+  int32_t tile_particles;   /* target mean particles per brick (the on-chip sort tile);
+                               0 = 640; see mpc_autotune */
+  int32_t threads_per_cell; /* threads that reduce one cell: 0 (auto) or a power of two
+                               <= 32; see mpc_autotune */
+  int32_t obs_ring;         /* rows of the per-step observables ring; 0 = 1024 */
+  int32_t reserved;         /* must be 0 */
 } mpc_params;
 
 /* Device-memory provider.  alloc returns device memory of `bytes` (>= 256-byte aligned)
@@ -115,7 +130,7 @@ typedef struct {
   int32_t n_bricks[3];
   uint64_t device_bytes; /* device memory held by the handle */
   int32_t recoveries;    /* capacity overflows repaired so far */
-  int32_t reserved;
+  int32_t threads_per_cell;
 } mpc_info;
 
 /* Create a box, initialise it (Sec. II: uniform positions, Maxwell-Boltzmann velocities
@@ -192,6 +207,94 @@ mpc_status mpc_profile_step_kernel(mpc_handle h, double* mean_ms, int32_t* sampl
 mpc_status mpc_sort_by_cell_noalloc(const int32_t L[3], int64_t n, const uint32_t* X,
                                     const float* V, const uint32_t* id, uint32_t* X_out,
                                     float* V_out, uint32_t* id_out, void* stream);
+
+/* Stop the box at step `limit`: later steps (single or batched) leave it unchanged.
+ * limit must not lie before the steps already requested (MPC_EINVAL).  Asynchronous.
+ * The paper runs one system per job and has no counterpart; batches and the serving
+ * loop use it to end each job at its own step count inside a shared step chain. */
+mpc_status mpc_set_step_limit(mpc_handle h, int64_t limit);
+
+/* Device bytes a box with parameters p holds while it lives (steady) and at most during
+ * mpc_create (peak), on the current device.  No allocation; MPC_EINVAL as mpc_create. */
+mpc_status mpc_footprint(const mpc_params* p, uint64_t* steady_bytes, uint64_t* peak_bytes);
+
+/* Picks tile_particles and threads_per_cell for boxes like p by timing the fused step
+ * kernel on a box with p's parameters (edges clipped so it holds about 8M particles):
+ * tiles of about 320, 640 and 1280 particles, each with the thread splits that finalise
+ * a brick in at most four passes.  Results are written to *tile_particles,
+ * *threads_per_cell and *ns_per_particle_step (the best time); the parameters chosen
+ * change only speed (with MPC_FLAG_DETERMINISTIC not even the rounding).  Allocates
+ * and frees device memory with cudaMalloc; synchronises `stream`. */
+mpc_status mpc_autotune(const mpc_params* p, void* stream, int32_t* tile_particles,
+                        int32_t* threads_per_cell, double* ns_per_particle_step);
+
+/* ---- Batches: many independent boxes advanced together ----------------------------
+ * The paper runs one system per job; a batch packs many boxes (any L, variant, alpha,
+ * h, n_c, seed) into one persistent launch of the fused step per time step, over the
+ * concatenated list of every box's bricks, inside CUDA graphs of graph_steps steps.
+ * Member boxes are ordinary handles (mpc_get_state, mpc_observables, ... work on them)
+ * created and destroyed through the batch; their device memory comes from the batch's
+ * arena when it has one.  A batch and its members are used by one host thread. */
+typedef struct mpc_batch_s* mpc_batch;
+
+enum {
+  MPC_BATCH_DETERMINISTIC = 1u,  /* members get MPC_FLAG_DETERMINISTIC */
+  MPC_BATCH_AUTOTUNE = 2u        /* members without explicit tile_particles /
+                                    threads_per_cell are tuned per class (variant,
+                                    n_c, thermostat, walls, flags) with mpc_autotune */
+};
+
+typedef struct {
+  uint64_t arena_bytes;  /* device memory for all members, allocated once; admission
+                            fails with MPC_ENOMEM when a box does not fit.  0: members
+                            allocate with cudaMalloc */
+  int32_t graph_steps;   /* batch steps per captured graph; 0 = 100 */
+  uint32_t flags;        /* MPC_BATCH_* */
+  int32_t max_boxes;     /* 0 = 4096 (the maximum) */
+  int32_t reserved;      /* must be 0 */
+} mpc_batch_config;
+
+typedef struct {
+  int32_t n_boxes;
+  int32_t work_items;       /* bricks over all members */
+  int64_t n_particles;
+  uint64_t arena_bytes, arena_used, arena_largest_free;
+  int32_t grid;             /* CTAs of the persistent step launch */
+  int32_t ctas_per_sm;
+  int32_t smem_bytes;       /* dynamic shared memory per CTA (largest member) */
+  int32_t graph_builds;
+  int32_t tuned_classes;
+  int32_t reserved;
+} mpc_batch_info;
+
+/* Create an empty batch on `stream` (cudaStream_t or NULL). */
+mpc_status mpc_batch_create(const mpc_batch_config* cfg, void* stream, mpc_batch* out);
+
+/* Destroy the batch and every member box (after finishing queued work). */
+mpc_status mpc_batch_destroy(mpc_batch b);
+
+/* Create a box (as mpc_create) and make it a member.  Its creation runs on a side
+ * stream of the batch, overlapping steps already queued; the box joins the steps
+ * enqueued after this call, starting from its step 0.  MPC_ENOMEM (nothing created)
+ * when the arena cannot hold it; MPC_EINVAL when the batch is full. */
+mpc_status mpc_batch_add(mpc_batch b, const mpc_params* p, mpc_handle* out);
+
+/* Remove a member and release it.  Its memory returns to the arena once the work
+ * queued before this call has finished; no synchronisation. */
+mpc_status mpc_batch_remove(mpc_batch b, mpc_handle h);
+
+/* Enqueue nsteps batch steps: every member advances by one step per batch step until
+ * it reaches its step limit (mpc_set_step_limit).  Asynchronous. */
+mpc_status mpc_batch_step(mpc_batch b, int64_t nsteps);
+
+/* Wait for queued steps, repair members whose brick capacity overflowed (they finish
+ * their steps alone), and report the first member error. */
+mpc_status mpc_batch_synchronize(mpc_batch b);
+
+mpc_status mpc_batch_get_info(mpc_batch b, mpc_batch_info* out);
+
+/* Text of the last error of a batch call (NULL: of the last failed mpc_batch_create). */
+const char* mpc_batch_last_error(mpc_batch b);
 
 /* Text of the last error on h (or of the last failed create when h is NULL). */
 const char* mpc_last_error(mpc_handle h);

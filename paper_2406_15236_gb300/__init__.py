@@ -21,7 +21,8 @@ _LIB_PATH = _build.LIB
 
 MPC_SRD, MPC_AT_A, MPC_SRD_A = 0, 1, 2
 MPC_OK, MPC_EINVAL, MPC_ENOMEM, MPC_ECUDA, MPC_ETIMEOUT, MPC_ESTATE = range(6)
-MPC_FLAG_OBSERVABLES, MPC_FLAG_DEBUG_CELLS = 1, 2
+MPC_FLAG_OBSERVABLES, MPC_FLAG_DEBUG_CELLS, MPC_FLAG_DETERMINISTIC = 1, 2, 4
+MPC_BATCH_DETERMINISTIC, MPC_BATCH_AUTOTUNE = 1, 2
 STATUS_NAMES = {0: "MPC_OK", 1: "MPC_EINVAL", 2: "MPC_ENOMEM", 3: "MPC_ECUDA",
                 4: "MPC_ETIMEOUT", 5: "MPC_ESTATE"}
 OBS_ROW = ["px", "py", "pz", "sum_v2", "skin_xy", "skin_yz", "skin_zx", "scol_xy", "scol_yx",
@@ -41,7 +42,9 @@ class mpc_params(ctypes.Structure):
                 ("thermostat", ctypes.c_int32), ("walls_z", ctypes.c_int32),
                 ("gravity", ctypes.c_double * 3), ("seed", ctypes.c_uint64),
                 ("box_id", ctypes.c_uint32), ("flags", ctypes.c_uint32),
-                ("capacity", ctypes.c_int32), ("graph_steps", ctypes.c_int32)]
+                ("capacity", ctypes.c_int32), ("graph_steps", ctypes.c_int32),
+                ("tile_particles", ctypes.c_int32), ("threads_per_cell", ctypes.c_int32),
+                ("obs_ring", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -66,7 +69,22 @@ class mpc_info(ctypes.Structure):
                 ("step", ctypes.c_int64), ("fixed_bits", ctypes.c_int32),
                 ("capacity", ctypes.c_int32), ("brick", ctypes.c_int32 * 3),
                 ("n_bricks", ctypes.c_int32 * 3), ("device_bytes", ctypes.c_uint64),
-                ("recoveries", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("recoveries", ctypes.c_int32), ("threads_per_cell", ctypes.c_int32)]
+
+
+class mpc_batch_config(ctypes.Structure):
+    _fields_ = [("arena_bytes", ctypes.c_uint64), ("graph_steps", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("max_boxes", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class mpc_batch_info(ctypes.Structure):
+    _fields_ = [("n_boxes", ctypes.c_int32), ("work_items", ctypes.c_int32),
+                ("n_particles", ctypes.c_int64), ("arena_bytes", ctypes.c_uint64),
+                ("arena_used", ctypes.c_uint64), ("arena_largest_free", ctypes.c_uint64),
+                ("grid", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("smem_bytes", ctypes.c_int32), ("graph_builds", ctypes.c_int32),
+                ("tuned_classes", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -100,13 +118,29 @@ def lib():
     L.mpc_profile_step_kernel.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_int32)]
     L.mpc_sort_by_cell_noalloc.argtypes = [P(ctypes.c_int32), ctypes.c_int64, vp, vp, vp, vp, vp,
                                            vp, vp]
+    L.mpc_set_step_limit.argtypes = [vp, ctypes.c_int64]
+    L.mpc_footprint.argtypes = [P(mpc_params), P(ctypes.c_uint64), P(ctypes.c_uint64)]
+    L.mpc_autotune.argtypes = [P(mpc_params), vp, P(ctypes.c_int32), P(ctypes.c_int32),
+                               P(ctypes.c_double)]
+    L.mpc_batch_create.argtypes = [P(mpc_batch_config), vp, P(vp)]
+    L.mpc_batch_destroy.argtypes = [vp]
+    L.mpc_batch_add.argtypes = [vp, P(mpc_params), P(vp)]
+    L.mpc_batch_remove.argtypes = [vp, vp]
+    L.mpc_batch_step.argtypes = [vp, ctypes.c_int64]
+    L.mpc_batch_synchronize.argtypes = [vp]
+    L.mpc_batch_get_info.argtypes = [vp, P(mpc_batch_info)]
+    L.mpc_batch_last_error.argtypes = [vp]
+    L.mpc_batch_last_error.restype = ctypes.c_char_p
     L.mpc_last_error.argtypes = [vp]
     L.mpc_last_error.restype = ctypes.c_char_p
     L.mpc_version.restype = ctypes.c_char_p
     for name in ("mpc_create", "mpc_destroy", "mpc_step", "mpc_synchronize", "mpc_get_state",
                  "mpc_set_state", "mpc_get_cell_counts", "mpc_observables",
                  "mpc_observable_series", "mpc_get_info", "mpc_set_profiling",
-                 "mpc_profile_step_kernel", "mpc_sort_by_cell_noalloc"):
+                 "mpc_profile_step_kernel", "mpc_sort_by_cell_noalloc", "mpc_set_step_limit",
+                 "mpc_footprint", "mpc_autotune", "mpc_batch_create", "mpc_batch_destroy",
+                 "mpc_batch_add", "mpc_batch_remove", "mpc_batch_step", "mpc_batch_synchronize",
+                 "mpc_batch_get_info"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -118,9 +152,16 @@ def _check(status, handle=None):
         raise MpcError(status, msg.decode() if msg else "")
 
 
+def _check_batch(status, batch=None):
+    if status != MPC_OK:
+        msg = lib().mpc_batch_last_error(batch)
+        raise MpcError(status, msg.decode() if msg else "")
+
+
 def make_params(L=(16, 16, 16), n_c=10.0, h=0.1, alpha_deg=130.0, kT=1.0, m=1.0,
                 variant=MPC_SRD, thermostat=0, walls_z=0, gravity=(0.0, 0.0, 0.0), seed=1,
-                box_id=0, flags=0, capacity=0, graph_steps=0) -> mpc_params:
+                box_id=0, flags=0, capacity=0, graph_steps=0, tile_particles=0,
+                threads_per_cell=0, obs_ring=0) -> mpc_params:
     if isinstance(L, int):
         L = (L, L, L)
     p = mpc_params()
@@ -131,6 +172,8 @@ def make_params(L=(16, 16, 16), n_c=10.0, h=0.1, alpha_deg=130.0, kT=1.0, m=1.0,
     p.gravity[:] = list(gravity)
     p.seed, p.box_id, p.flags = seed, box_id, flags
     p.capacity, p.graph_steps = capacity, graph_steps
+    p.tile_particles, p.threads_per_cell, p.obs_ring = tile_particles, threads_per_cell, obs_ring
+    p.reserved = 0
     return p
 
 
@@ -254,21 +297,74 @@ def mpc_sort_by_cell_noalloc(L, n, X, V, ids, X_out, V_out, ids_out, stream=None
                                           _addr(V_out), _addr(ids_out), ctypes.c_void_p(stream or 0)))
 
 
+def mpc_set_step_limit(handle, limit: int) -> None:
+    _check(lib().mpc_set_step_limit(handle, int(limit)), handle)
+
+
+def mpc_footprint(params: mpc_params):
+    """(steady, peak) device bytes of a box with these parameters."""
+    s, p = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().mpc_footprint(ctypes.byref(params), ctypes.byref(s), ctypes.byref(p)))
+    return s.value, p.value
+
+
+def mpc_autotune(params: mpc_params, stream=None):
+    """(tile_particles, threads_per_cell, ns per particle-step) picked by timing."""
+    t, c, ns = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    _check(lib().mpc_autotune(ctypes.byref(params), ctypes.c_void_p(stream or 0), ctypes.byref(t),
+                              ctypes.byref(c), ctypes.byref(ns)))
+    return t.value, c.value, ns.value
+
+
+def mpc_batch_create(config: mpc_batch_config | None = None, stream=None):
+    b = ctypes.c_void_p()
+    _check_batch(lib().mpc_batch_create(ctypes.byref(config) if config is not None else None,
+                                        ctypes.c_void_p(stream or 0), ctypes.byref(b)))
+    return b
+
+
+def mpc_batch_destroy(batch) -> None:
+    _check_batch(lib().mpc_batch_destroy(batch), batch)
+
+
+def mpc_batch_add(batch, params: mpc_params):
+    h = ctypes.c_void_p()
+    _check_batch(lib().mpc_batch_add(batch, ctypes.byref(params), ctypes.byref(h)), batch)
+    return h
+
+
+def mpc_batch_remove(batch, handle) -> None:
+    _check_batch(lib().mpc_batch_remove(batch, handle), batch)
+
+
+def mpc_batch_step(batch, nsteps: int) -> None:
+    _check_batch(lib().mpc_batch_step(batch, int(nsteps)), batch)
+
+
+def mpc_batch_synchronize(batch) -> None:
+    _check_batch(lib().mpc_batch_synchronize(batch), batch)
+
+
+def mpc_batch_get_info(batch) -> mpc_batch_info:
+    i = mpc_batch_info()
+    _check_batch(lib().mpc_batch_get_info(batch, ctypes.byref(i)), batch)
+    return i
+
+
+def mpc_batch_last_error(batch=None) -> str:
+    s = lib().mpc_batch_last_error(batch)
+    return s.decode() if s else ""
+
+
 # --- convenience wrapper -----------------------------------------------------------------
 
-class Simulation:
-    """One MPC box on the current CUDA device."""
+class Box:
+    """State access for one MPC box (a standalone Simulation or a batch member)."""
 
-    def __init__(self, stream=None, use_torch_allocator=True, **kw):
-        import torch
-
-        self.params = make_params(**kw)
-        if stream is None:
-            stream = torch.cuda.current_stream().cuda_stream
-        self.stream = stream
-        self._alloc = torch_allocator() if use_torch_allocator else None
-        self.handle = mpc_create(self.params, stream, self._alloc)
-        self.info = mpc_get_info(self.handle)
+    def __init__(self, handle, params: mpc_params):
+        self.handle = handle
+        self.params = params
+        self.info = mpc_get_info(handle)
         self.N = self.info.n_particles
 
     def step(self, n: int = 1):
@@ -276,6 +372,9 @@ class Simulation:
 
     def synchronize(self):
         mpc_synchronize(self.handle)
+
+    def set_step_limit(self, limit: int):
+        mpc_set_step_limit(self.handle, limit)
 
     def get_state(self, cells=False):
         """(X (3,N) uint32, V (3,N) float32, ids (N,), step[, cell]) on the host, sorted by
@@ -311,10 +410,85 @@ class Simulation:
         n = mpc_observable_series(self.handle, rows)
         return rows[:n]
 
+
+class Simulation(Box):
+    """One MPC box on the current CUDA device."""
+
+    def __init__(self, stream=None, use_torch_allocator=True, **kw):
+        import torch
+
+        params = make_params(**kw)
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        self._alloc = torch_allocator() if use_torch_allocator else None
+        super().__init__(mpc_create(params, stream, self._alloc), params)
+
     def close(self):
         if self.handle is not None:
             mpc_destroy(self.handle)
             self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """Many independent boxes advanced together by one persistent launch per step."""
+
+    def __init__(self, arena_bytes=0, graph_steps=0, deterministic=False, autotune=False,
+                 max_boxes=0, stream=None):
+        import torch
+
+        cfg = mpc_batch_config()
+        cfg.arena_bytes = int(arena_bytes)
+        cfg.graph_steps = int(graph_steps)
+        cfg.flags = (MPC_BATCH_DETERMINISTIC if deterministic else 0) | \
+            (MPC_BATCH_AUTOTUNE if autotune else 0)
+        cfg.max_boxes = int(max_boxes)
+        cfg.reserved = 0
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        self.handle = mpc_batch_create(cfg, stream)
+        self.boxes: list[Box] = []
+
+    def add(self, **kw) -> Box:
+        params = make_params(**kw)
+        box = Box(mpc_batch_add(self.handle, params), params)
+        self.boxes.append(box)
+        return box
+
+    def remove(self, box: Box) -> None:
+        mpc_batch_remove(self.handle, box.handle)
+        self.boxes.remove(box)
+        box.handle = None
+
+    def step(self, n: int = 1) -> None:
+        mpc_batch_step(self.handle, n)
+
+    def synchronize(self) -> None:
+        mpc_batch_synchronize(self.handle)
+
+    def info(self) -> mpc_batch_info:
+        return mpc_batch_get_info(self.handle)
+
+    def close(self):
+        if self.handle is not None:
+            mpc_batch_destroy(self.handle)
+            self.handle = None
+            for b in self.boxes:
+                b.handle = None
+            self.boxes = []
 
     def __del__(self):
         try:

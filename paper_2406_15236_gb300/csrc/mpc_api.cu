@@ -11,67 +11,32 @@
 #include <vector>
 
 #include "mpc.h"
+#include "mpc_host.h"
 #include "mpc_internal.h"
 
 using namespace mpc;
-
-struct mpc_s {
-  mpc_params p{};
-  Geom g{};
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  cudaStream_t cap_stream = nullptr;
-  mpc_allocator alloc{};
-  bool has_alloc = false;
-  int64_t N = 0;
-  PBuf buf[2]{};
-  uint32_t* cnt[2]{};
-  Ctrl* ctrl = nullptr;
-  Ctrl* ctrl_host = nullptr;  // pinned mirror
-  Spill spill{};
-  double* obs_partials = nullptr;
-  double* obs_series = nullptr;
-  int obs_ring = 1024;
-  uint32_t* dbg_counts = nullptr;
-  int64_t target_step = 0;
-  cudaGraphExec_t graph = nullptr;
-  int graph_steps = 16;
-  int recoveries = 0;
-  size_t smem_limit = 0;
-  // profiling: event pairs around step-kernel launches (graph nodes and single launches)
-  bool profiling = false;
-  std::vector<cudaEvent_t> ev_begin, ev_end;
-  int ev_next = 0;       // next slot for a single launch
-  int ev_recorded = 0;   // valid pairs
-  std::string err;
-  std::vector<std::pair<void*, size_t>> allocs;
-  size_t bytes = 0;
-};
+using namespace mpc::host;
 
 namespace {
-
 thread_local std::string g_last_create_error;
+}  // namespace
 
-const char* kVersion = "mpc-gb300 0.1 (sm_103a)";
-
+namespace mpc {
+namespace host {
 mpc_status fail(mpc_handle h, mpc_status st, const std::string& msg) {
   if (h) h->err = msg;
   else g_last_create_error = msg;
   return st;
 }
+}  // namespace host
+}  // namespace mpc
 
-#define CU(h, call)                                                                        \
-  do {                                                                                     \
-    cudaError_t e_ = (call);                                                               \
-    if (e_ != cudaSuccess)                                                                 \
-      return fail((h), MPC_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
-  } while (0)
+namespace {
+const char* kVersion = "mpc-gb300 0.2 (sm_103a)";
+}  // namespace
 
-#define TRY(expr)                    \
-  do {                               \
-    mpc_status s_ = (expr);          \
-    if (s_ != MPC_OK) return s_;     \
-  } while (0)
+namespace mpc {
+namespace host {
 
 void* dev_alloc(mpc_handle h, size_t bytes) {
   if (bytes == 0) bytes = 256;
@@ -120,18 +85,20 @@ int ceil_log2(int v) {
 }
 
 // derived brick quantities: log2 of the edges, counts, threads per cell
-void finish_bricks(Geom& g) {
+// tpc_req > 0 fixes the threads per cell; 0 picks the largest power of two that still
+// finalises every cell of the brick in one pass
+void finish_bricks(Geom& g, int tpc_req) {
   for (int ax = 0; ax < 3; ++ax) g.Bs[ax] = ceil_log2(g.B[ax]);
   g.nbricks = g.nb[0] * g.nb[1] * g.nb[2];
   g.brick_cells = g.B[0] * g.B[1] * g.B[2];
   int tpc = 1;
   while (tpc < 32 && tpc * 2 * g.brick_cells <= kStepThreads) tpc *= 2;
-  g.tpc = tpc;
+  g.tpc = tpc_req > 0 ? tpc_req : tpc;
 }
 
-// cells per brick: powers of two, grown on the shortest axis first, ~kBrickParticles
-void choose_bricks(Geom& g, double n_c) {
-  const int target = std::max(1, (int)std::lround(kBrickParticles / std::max(n_c, 1e-3)));
+// cells per brick: powers of two, grown on the shortest axis first, ~tile particles
+void choose_bricks(Geom& g, double n_c, int tile, int tpc_req) {
+  const int target = std::max(1, (int)std::lround(tile / std::max(n_c, 1e-3)));
   int B[3] = {1, 1, 1};
   for (;;) {
     int best = -1;
@@ -144,7 +111,7 @@ void choose_bricks(Geom& g, double n_c) {
     g.B[ax] = B[ax];
     g.nb[ax] = (g.Lc[ax] + B[ax] - 1) / B[ax];
   }
-  finish_bricks(g);
+  finish_bricks(g, tpc_req);
 }
 
 int capacity_for(double mean) {
@@ -174,6 +141,18 @@ mpc_status validate(const mpc_params* p) {
   if (N < 1 || N > 4.0e9) return fail(nullptr, MPC_EINVAL, "particle count must lie in [1, 4e9]");
   if (p->capacity < 0 || p->capacity > 60000) return fail(nullptr, MPC_EINVAL, "capacity must lie in [0, 60000]");
   if (p->graph_steps < 0) return fail(nullptr, MPC_EINVAL, "graph_steps must be >= 0");
+  if (p->tile_particles < 0 || p->tile_particles > 16384)
+    return fail(nullptr, MPC_EINVAL, "tile_particles must lie in [0, 16384]");
+  {
+    const int t = p->threads_per_cell;
+    if (t < 0 || t > 32 || (t & (t - 1)) != 0)
+      return fail(nullptr, MPC_EINVAL, "threads_per_cell must be 0 or a power of two <= 32");
+  }
+  if (p->reserved != 0) return fail(nullptr, MPC_EINVAL, "reserved must be 0");
+  if (p->obs_ring < 0 || p->obs_ring > (1 << 24))
+    return fail(nullptr, MPC_EINVAL, "obs_ring must lie in [0, 2^24]");
+  if (p->flags & ~(uint32_t)(MPC_FLAG_OBSERVABLES | MPC_FLAG_DEBUG_CELLS | MPC_FLAG_DETERMINISTIC))
+    return fail(nullptr, MPC_EINVAL, "unknown flag bits");
   return MPC_OK;
 }
 
@@ -206,6 +185,7 @@ void free_particle_buffers(mpc_handle h) {
 }
 
 mpc_status alloc_particle_buffers(mpc_handle h) {
+  h->buffers_gen += 1;  // step arguments captured elsewhere (graphs, batch tables) are stale
   const size_t n = (size_t)h->g.nbricks * (size_t)h->g.cap;
   for (int s = 0; s < 2; ++s) {
     for (int ax = 0; ax < 3; ++ax) {
@@ -248,6 +228,8 @@ mpc_status check_errors(mpc_handle h) {
   if (c.errors & kErrTimeout) return fail(h, MPC_ETIMEOUT, "a bounded device wait gave up (bulk copy)");
   if (c.errors & kErrBinning) return fail(h, MPC_ESTATE, "a particle was found outside its brick");
   if (c.errors & kErrRange) return fail(h, MPC_ESTATE, "a position outside the box was found");
+  if (c.errors & kErrFixedRange)
+    return fail(h, MPC_ESTATE, "a fixed-point cell-sum term exceeded its range (2^15)");
   if (c.lost) return fail(h, MPC_ESTATE, "brick and spill capacity both overflowed; state lost");
   return MPC_OK;
 }
@@ -299,6 +281,8 @@ mpc_status bin_into_bricks(mpc_handle h, const PBuf& src, int64_t n, int64_t ste
 mpc_status reset_ctrl(mpc_handle h, int64_t step) {
   Ctrl c{};
   c.step = step;
+  h->limit = std::max(h->limit, step);
+  c.limit = h->limit;
   *h->ctrl_host = c;
   CU(h, cudaMemcpyAsync(h->ctrl, h->ctrl_host, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
   CU(h, cudaStreamSynchronize(h->stream));
@@ -453,52 +437,18 @@ mpc_status set_device(mpc_handle h) {
   return MPC_OK;
 }
 
-}  // namespace
-
-namespace mpc {
-// lets entry points that take no handle report through mpc_last_error(NULL)
-void set_null_handle_error(const std::string& msg) { g_last_create_error = msg; }
-}  // namespace mpc
-
-extern "C" {
-
-const char* mpc_version(void) { return kVersion; }
-
-const char* mpc_last_error(mpc_handle h) {
-  return h ? h->err.c_str() : g_last_create_error.c_str();
+size_t device_smem_limit(int device) {
+  int optin = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return (size_t)optin - 2048;  // room for the kernel's static shared memory
 }
 
-mpc_status mpc_create(const mpc_params* p, void* stream, const mpc_allocator* alloc, mpc_handle* out) {
-  if (!out) return fail(nullptr, MPC_EINVAL, "out is NULL");
-  *out = nullptr;
+mpc_status plan_box(const mpc_params* p, size_t smem_limit, Geom& g, int64_t& N) {
   TRY(validate(p));
-  if (alloc && (!alloc->alloc || !alloc->release))
-    return fail(nullptr, MPC_EINVAL, "allocator needs alloc and release");
-  mpc_handle h = new (std::nothrow) mpc_s();
-  if (!h) return fail(nullptr, MPC_ENOMEM, "host allocation failed");
-  auto bail = [&](mpc_status st) {
-    g_last_create_error = h->err;
-    mpc_destroy(h);
-    return st;
-  };
-  h->p = *p;
-  if (cudaGetDevice(&h->device) != cudaSuccess) {
-    cudaGetLastError();
-    delete h;
-    return fail(nullptr, MPC_ECUDA, "no CUDA device");
-  }
-  h->stream = static_cast<cudaStream_t>(stream);
-  if (alloc) {
-    h->alloc = *alloc;
-    h->has_alloc = true;
-  }
-  if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
-    return bail(fail(h, MPC_ECUDA, "stream creation failed"));
-  if (cudaMallocHost(&h->ctrl_host, sizeof(Ctrl)) != cudaSuccess)
-    return bail(fail(h, MPC_ENOMEM, "pinned host allocation failed"));
-  h->graph_steps = p->graph_steps > 0 ? p->graph_steps : 16;
-
-  Geom& g = h->g;
+  g = Geom{};
   int lmax = std::max(p->L[0], std::max(p->L[1], p->L[2]));
   g.F = 31 - ceil_log2(lmax);
   g.mask = (1u << g.F) - 1u;
@@ -526,34 +476,94 @@ mpc_status mpc_create(const mpc_params* p, void* stream, const mpc_allocator* al
   g.box = p->box_id;
   g.obs = (p->flags & MPC_FLAG_OBSERVABLES) ? 1 : 0;
   g.debug = (p->flags & MPC_FLAG_DEBUG_CELLS) ? 1 : 0;
+  g.det = (p->flags & MPC_FLAG_DETERMINISTIC) ? 1 : 0;
   g.ncells = (int64_t)g.Lc[0] * g.Lc[1] * g.Lc[2];
-  choose_bricks(g, p->n_c);
+  const int tile = p->tile_particles > 0 ? p->tile_particles : kBrickParticles;
+  choose_bricks(g, p->n_c, tile, p->threads_per_cell);
   g.cap = p->capacity > 0 ? ((p->capacity + 3) & ~3) : capacity_for(p->n_c * g.brick_cells);
-  {
-    int optin = 0;
-    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device) != cudaSuccess)
-      return bail(fail(h, MPC_ECUDA, "cannot query shared memory per block"));
-    h->smem_limit = (size_t)optin - 2048;  // room for the kernel's static shared memory
-    // shrink the brick until one brick's particles fit in shared memory
-    while (step_smem_bytes(g) > h->smem_limit && g.brick_cells > 1 && p->capacity == 0) {
-      int ax = 0;
-      for (int k = 1; k < 3; ++k)
-        if (g.B[k] > g.B[ax]) ax = k;
-      g.B[ax] /= 2;
-      g.nb[ax] = (g.Lc[ax] + g.B[ax] - 1) / g.B[ax];
-      finish_bricks(g);
-      g.cap = capacity_for(p->n_c * g.brick_cells);
-    }
-    if (step_smem_bytes(g) > h->smem_limit)
-      return bail(fail(h, MPC_EINVAL, "brick capacity exceeds shared memory"));
+  // shrink the brick until one brick's particles fit in shared memory
+  while (step_smem_bytes(g) > smem_limit && g.brick_cells > 1 && p->capacity == 0) {
+    int ax = 0;
+    for (int k = 1; k < 3; ++k)
+      if (g.B[k] > g.B[ax]) ax = k;
+    g.B[ax] /= 2;
+    g.nb[ax] = (g.Lc[ax] + g.B[ax] - 1) / g.B[ax];
+    finish_bricks(g, p->threads_per_cell);
+    g.cap = capacity_for(p->n_c * g.brick_cells);
   }
-  h->N = std::llround((double)p->L[0] * p->L[1] * p->L[2] * p->n_c);
+  if (step_smem_bytes(g) > smem_limit) return fail(nullptr, MPC_EINVAL, "brick capacity exceeds shared memory");
+  N = std::llround((double)p->L[0] * p->L[1] * p->L[2] * p->n_c);
+  return MPC_OK;
+}
+
+namespace {
+size_t rounded(size_t bytes) { return ((bytes ? bytes : 256) + 255) & ~size_t(255); }
+uint32_t spill_capacity(int64_t N) { return (uint32_t)std::max<int64_t>(4096, N / 256); }
+}  // namespace
+
+void box_footprint(const Geom& g, int64_t N, size_t& steady, size_t& peak) {
+  const size_t n = (size_t)g.nbricks * (size_t)g.cap;
+  const size_t sp = spill_capacity(N);
+  size_t s = rounded(sizeof(Ctrl)) + 2 * rounded((size_t)g.nbricks * 4);
+  s += 8 * rounded(sp * 4) + (g.debug ? rounded(sp * 4) : 0);  // x, v, id, dest (+ cell)
+  s += rounded(sizeof(double) * kObsSlots * kObsWidth);
+  if (g.debug) s += rounded((size_t)g.ncells * 4);
+  s += 2 * (7 + (g.debug ? 1 : 0)) * rounded(n * 4);
+  steady = s;
+  // creation: contiguous staging (7 arrays) + init sums + bin counts
+  const size_t a = ((size_t)N * 4 + 255) & ~size_t(255);
+  peak = s + rounded(a * 7) + rounded(sizeof(double) * 3 * 64) + rounded(((size_t)g.nbricks + 1) * 4);
+}
+
+mpc_status create_box(const mpc_params* p, cudaStream_t stream, const mpc_allocator* alloc,
+                      Ctrl* ctrl_slot, mpc_handle* out) {
+  if (!out) return fail(nullptr, MPC_EINVAL, "out is NULL");
+  *out = nullptr;
+  TRY(validate(p));
+  if (alloc && (!alloc->alloc || !alloc->release))
+    return fail(nullptr, MPC_EINVAL, "allocator needs alloc and release");
+  mpc_handle h = new (std::nothrow) mpc_s();
+  if (!h) return fail(nullptr, MPC_ENOMEM, "host allocation failed");
+  auto bail = [&](mpc_status st) {
+    g_last_create_error = h->err;
+    destroy_box(h, true);
+    return st;
+  };
+  h->p = *p;
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return fail(nullptr, MPC_ECUDA, "no CUDA device");
+  }
+  h->stream = stream;
+  if (alloc) {
+    h->alloc = *alloc;
+    h->has_alloc = true;
+  }
+  if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(fail(h, MPC_ECUDA, "stream creation failed"));
+  if (ctrl_slot) {
+    h->ctrl_host = ctrl_slot;
+    h->ctrl_host_owned = false;
+  } else if (cudaMallocHost(&h->ctrl_host, sizeof(Ctrl)) != cudaSuccess) {
+    h->ctrl_host = nullptr;
+    return bail(fail(h, MPC_ENOMEM, "pinned host allocation failed"));
+  }
+  h->graph_steps = p->graph_steps > 0 ? p->graph_steps : 16;
+  h->obs_ring = p->obs_ring > 0 ? p->obs_ring : 1024;
+  h->smem_limit = device_smem_limit(h->device);
+  if (h->smem_limit == 0) return bail(fail(h, MPC_ECUDA, "cannot query shared memory per block"));
+  {
+    mpc_status st = plan_box(p, h->smem_limit, h->g, h->N);
+    if (st != MPC_OK) return bail(fail(h, st, g_last_create_error));
+  }
+  Geom& g = h->g;
 
   mpc_status st;
   if ((st = alloc_array(h, &h->ctrl, 1, "control block")) != MPC_OK) return bail(st);
   for (int s = 0; s < 2; ++s)
     if ((st = alloc_array(h, &h->cnt[s], (size_t)g.nbricks, "brick counts")) != MPC_OK) return bail(st);
-  h->spill.capacity = (uint32_t)std::max<int64_t>(4096, h->N / 256);
+  h->spill.capacity = spill_capacity(h->N);
   for (int ax = 0; ax < 3; ++ax) {
     if ((st = alloc_array(h, &h->spill.x[ax], h->spill.capacity, "spill")) != MPC_OK) return bail(st);
     if ((st = alloc_array(h, &h->spill.v[ax], h->spill.capacity, "spill")) != MPC_OK) return bail(st);
@@ -590,17 +600,50 @@ mpc_status mpc_create(const mpc_params* p, void* stream, const mpc_allocator* al
   return MPC_OK;
 }
 
-mpc_status mpc_destroy(mpc_handle h) {
-  if (!h) return MPC_OK;
+void destroy_box(mpc_handle h, bool sync) {
+  if (!h) return;
   cudaSetDevice(h->device);
-  cudaStreamSynchronize(h->stream);
+  if (sync) cudaStreamSynchronize(h->stream);
   if (h->graph) cudaGraphExecDestroy(h->graph);
   for (cudaEvent_t e : h->ev_begin) cudaEventDestroy(e);
   for (cudaEvent_t e : h->ev_end) cudaEventDestroy(e);
   while (!h->allocs.empty()) dev_free(h, h->allocs.back().first);
-  if (h->ctrl_host) cudaFreeHost(h->ctrl_host);
+  if (h->ctrl_host && h->ctrl_host_owned) cudaFreeHost(h->ctrl_host);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
+}
+
+mpc_status set_step_limit(mpc_handle h, int64_t limit) {
+  if (limit < h->target_step) return fail(h, MPC_EINVAL, "the limit lies before the steps already requested");
+  h->limit = limit;
+  CU(h, launch_store_i64(&h->ctrl->limit, limit, h->stream));
+  return MPC_OK;
+}
+
+}  // namespace host
+}  // namespace mpc
+
+namespace mpc {
+// lets entry points that take no handle report through mpc_last_error(NULL)
+void set_null_handle_error(const std::string& msg) { g_last_create_error = msg; }
+}  // namespace mpc
+
+extern "C" {
+
+const char* mpc_version(void) { return kVersion; }
+
+const char* mpc_last_error(mpc_handle h) {
+  return h ? h->err.c_str() : g_last_create_error.c_str();
+}
+
+mpc_status mpc_create(const mpc_params* p, void* stream, const mpc_allocator* alloc, mpc_handle* out) {
+  return create_box(p, static_cast<cudaStream_t>(stream), alloc, nullptr, out);
+}
+
+mpc_status mpc_destroy(mpc_handle h) {
+  if (!h) return MPC_OK;
+  if (h->batch) return fail(h, MPC_EINVAL, "the box belongs to a batch: use mpc_batch_remove");
+  destroy_box(h, true);
   return MPC_OK;
 }
 
@@ -608,8 +651,34 @@ mpc_status mpc_step(mpc_handle h, int64_t nsteps) {
   if (!h) return fail(nullptr, MPC_EINVAL, "handle is NULL");
   if (nsteps < 0) return fail(h, MPC_EINVAL, "nsteps must be >= 0");
   TRY(set_device(h));
-  h->target_step += nsteps;
-  return enqueue_steps(h, nsteps);
+  const int64_t n = std::min(nsteps, h->limit - h->target_step);
+  h->target_step += n;
+  return enqueue_steps(h, n);
+}
+
+mpc_status mpc_set_step_limit(mpc_handle h, int64_t limit) {
+  if (!h) return fail(nullptr, MPC_EINVAL, "handle is NULL");
+  TRY(set_device(h));
+  return set_step_limit(h, limit);
+}
+
+mpc_status mpc_footprint(const mpc_params* p, uint64_t* steady_bytes, uint64_t* peak_bytes) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, MPC_ECUDA, "no CUDA device");
+  }
+  const size_t lim = device_smem_limit(dev);
+  if (lim == 0) return fail(nullptr, MPC_ECUDA, "cannot query shared memory per block");
+  Geom g;
+  int64_t N = 0;
+  TRY(plan_box(p, lim, g, N));
+  size_t steady = 0, peak = 0;
+  box_footprint(g, N, steady, peak);
+  const size_t ring = (((size_t)(p->obs_ring > 0 ? p->obs_ring : 1024) * kObsWidth * 8) + 255) & ~size_t(255);
+  if (steady_bytes) *steady_bytes = steady + ring;
+  if (peak_bytes) *peak_bytes = peak + ring;
+  return MPC_OK;
 }
 
 mpc_status mpc_synchronize(mpc_handle h) {
@@ -840,6 +909,7 @@ mpc_status mpc_get_info(mpc_handle h, mpc_info* out) {
   }
   out->device_bytes = h->bytes;
   out->recoveries = h->recoveries;
+  out->threads_per_cell = h->g.tpc;
   return MPC_OK;
 }
 

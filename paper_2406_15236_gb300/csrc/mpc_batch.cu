@@ -1,0 +1,594 @@
+// Batches of independent MPC boxes (C ABI in include/mpc.h) and the kernel autotuner.
+//
+// A batch keeps a device work table (BatchTable): the step arguments of every member
+// and the prefix of their brick counts.  One persistent launch of the fused step kernel
+// per time step strides over all members' bricks; a second small launch closes the step
+// of every member.  Both are captured in a CUDA graph of graph_steps steps that reads
+// the table through a fixed pointer, so adding or removing members only rewrites the
+// table (a stream-ordered copy) -- the graph is rebuilt only when the largest member's
+// shared-memory need changes.
+//
+// Member device memory can come from one arena allocated up front.  Memory a member
+// releases returns to the arena only after the stream it was released on has passed the
+// release point (an event per release), so a member can be removed while steps that
+// still read it are queued.
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "mpc.h"
+#include "mpc_host.h"
+#include "mpc_internal.h"
+
+using namespace mpc;
+using namespace mpc::host;
+
+namespace {
+
+thread_local std::string g_batch_create_error;
+
+// First/best-fit suballocator over one device allocation with deferred release.
+class Arena {
+ public:
+  ~Arena() {
+    reclaim(true);
+    for (cudaEvent_t e : events_) cudaEventDestroy(e);
+    if (base_) cudaFree(base_);
+  }
+
+  bool init(size_t bytes) {
+    bytes &= ~size_t(255);
+    if (bytes == 0) return false;
+    if (cudaMalloc(&base_, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      base_ = nullptr;
+      return false;
+    }
+    size_ = bytes;
+    free_[0] = bytes;
+    return true;
+  }
+
+  void* alloc(size_t bytes) {
+    bytes = (bytes + 255) & ~size_t(255);
+    reclaim(false);
+    void* p = take(bytes);
+    if (!p && !pending_.empty()) {
+      reclaim(true);
+      p = take(bytes);
+    }
+    return p;
+  }
+
+  void release(void* p, size_t bytes, cudaStream_t s) {
+    bytes = (bytes + 255) & ~size_t(255);
+    const size_t off = static_cast<char*>(p) - static_cast<char*>(base_);
+    cudaEvent_t e = event();
+    if (e && cudaEventRecord(e, s) == cudaSuccess) {
+      pending_.push_back({off, bytes, e});
+    } else {
+      cudaGetLastError();
+      cudaStreamSynchronize(s);
+      if (e) events_.push_back(e);
+      give_back(off, bytes);
+    }
+  }
+
+  // returns released blocks whose streams have passed the release (wait: all of them)
+  void reclaim(bool wait) {
+    size_t k = 0;
+    while (k < pending_.size()) {
+      Pending& q = pending_[k];
+      const cudaError_t r = wait ? cudaEventSynchronize(q.ev) : cudaEventQuery(q.ev);
+      if (r == cudaSuccess) {
+        give_back(q.off, q.len);
+        events_.push_back(q.ev);
+        pending_[k] = pending_.back();
+        pending_.pop_back();
+      } else {
+        if (r != cudaErrorNotReady) cudaGetLastError();
+        ++k;
+      }
+    }
+  }
+
+  size_t size() const { return size_; }
+  size_t used() const { return used_; }
+  size_t pending() const {
+    size_t b = 0;
+    for (const Pending& q : pending_) b += q.len;
+    return b;
+  }
+  size_t largest_free() const {
+    size_t m = 0;
+    for (const auto& kv : free_) m = std::max(m, kv.second);
+    return m;
+  }
+
+ private:
+  struct Pending {
+    size_t off, len;
+    cudaEvent_t ev;
+  };
+
+  void* take(size_t bytes) {
+    auto best = free_.end();
+    for (auto it = free_.begin(); it != free_.end(); ++it)
+      if (it->second >= bytes && (best == free_.end() || it->second < best->second)) best = it;
+    if (best == free_.end()) return nullptr;
+    const size_t off = best->first, len = best->second;
+    free_.erase(best);
+    if (len > bytes) free_[off + bytes] = len - bytes;
+    used_ += bytes;
+    return static_cast<char*>(base_) + off;
+  }
+
+  void give_back(size_t off, size_t len) {
+    used_ -= len;
+    auto it = free_.emplace(off, len).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+
+  cudaEvent_t event() {
+    if (!events_.empty()) {
+      cudaEvent_t e = events_.back();
+      events_.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return e;
+  }
+
+  void* base_ = nullptr;
+  size_t size_ = 0, used_ = 0;
+  std::map<size_t, size_t> free_;  // offset -> length, coalesced
+  std::vector<Pending> pending_;
+  std::vector<cudaEvent_t> events_;
+};
+
+void* arena_alloc(void* ctx, size_t bytes, void*) { return static_cast<Arena*>(ctx)->alloc(bytes); }
+void arena_release(void* ctx, void* p, size_t bytes, void* stream) {
+  static_cast<Arena*>(ctx)->release(p, bytes, static_cast<cudaStream_t>(stream));
+}
+
+constexpr int kTableBuffers = 3;  // pinned host copies of the work table in rotation
+
+}  // namespace
+
+struct mpc_batch_s {
+  int device = 0;
+  cudaStream_t stream = nullptr;      // steps
+  cudaStream_t adm_stream = nullptr;  // member creation (overlaps queued steps)
+  cudaStream_t cap_stream = nullptr;  // graph capture
+  bool det = false, autotune = false;
+  int graph_steps = 100;
+  int max_boxes = kMaxBatchBoxes;
+  Arena* arena = nullptr;
+  mpc_allocator alloc{};
+  std::vector<mpc_handle> boxes;
+  std::vector<uint64_t> gens;  // buffers_gen of each member at the last table upload
+  Ctrl* ctrl_slab = nullptr;  // pinned control mirrors, one slot per member
+  std::vector<int> free_slots;
+  std::map<mpc_handle, int> slot_of;
+  BatchTable* table_dev = nullptr;
+  BatchTable* table_host[kTableBuffers] = {};
+  cudaEvent_t table_ev[kTableBuffers] = {};
+  bool table_ev_live[kTableBuffers] = {};
+  int table_next = 0;
+  bool dirty = true;
+  int total_items = 0;
+  int64_t total_particles = 0;
+  int num_sms = 0;
+  size_t smem = 0;
+  int ctas_per_sm = 0, grid = 0, adv_grid = 0;
+  cudaGraphExec_t graph = nullptr;
+  size_t graph_smem = 0;
+  int graph_grid = 0;
+  int graph_builds = 0;
+  std::map<std::string, std::pair<int, int>> tuned;
+  std::string err;
+};
+
+namespace {
+
+mpc_status bfail(mpc_batch b, mpc_status st, const std::string& msg) {
+  if (b) b->err = msg;
+  else g_batch_create_error = msg;
+  return st;
+}
+
+#define BCU(b, call)                                                                        \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return bfail((b), MPC_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
+  } while (0)
+
+size_t table_bytes(int nboxes) {
+  return offsetof(BatchTable, args) + sizeof(StepArgs) * (size_t)nboxes;
+}
+
+// Rewrites the device work table when members or their buffers changed; reconfigures
+// the persistent kernel when the largest shared-memory need changed.
+mpc_status refresh(mpc_batch b) {
+  // a member repaired or re-binned through its own handle has new buffers
+  for (size_t i = 0; i < b->boxes.size() && !b->dirty; ++i)
+    if (b->gens[i] != b->boxes[i]->buffers_gen) b->dirty = true;
+  if (!b->dirty) return MPC_OK;
+  // a pinned buffer whose previous upload has executed
+  const int k = b->table_next;
+  b->table_next = (k + 1) % kTableBuffers;
+  if (b->table_ev_live[k]) BCU(b, cudaEventSynchronize(b->table_ev[k]));
+  BatchTable* t = b->table_host[k];
+  const int n = (int)b->boxes.size();
+  t->nboxes = n;
+  int64_t items = 0, parts = 0;
+  size_t smem = 0;
+  for (int i = 0; i < n; ++i) {
+    mpc_handle h = b->boxes[(size_t)i];
+    t->begin[i] = (int32_t)items;
+    items += h->g.nbricks;
+    parts += h->N;
+    t->args[i] = step_args(h);
+    b->gens[(size_t)i] = h->buffers_gen;
+    smem = std::max(smem, step_smem_bytes(h->g));
+  }
+  if (items > INT32_MAX) return bfail(b, MPC_EINVAL, "the batch holds more than 2^31 bricks");
+  t->begin[n] = (int32_t)items;
+  t->total = (int32_t)items;
+  b->total_items = (int)items;
+  b->total_particles = parts;
+  BCU(b, cudaMemcpyAsync(b->table_dev, t, table_bytes(n), cudaMemcpyHostToDevice, b->stream));
+  BCU(b, cudaEventRecord(b->table_ev[k], b->stream));
+  b->table_ev_live[k] = true;
+  if (n > 0 && smem != b->smem) {
+    int per_sm = 0;
+    BCU(b, configure_batch_kernel(b->det, smem, &per_sm));
+    if (per_sm < 1) return bfail(b, MPC_EINVAL, "the batched step kernel does not fit on an SM");
+    b->smem = smem;
+    b->ctas_per_sm = per_sm;
+    b->grid = per_sm * b->num_sms;
+  }
+  b->dirty = false;
+  return MPC_OK;
+}
+
+mpc_status build_graph(mpc_batch b) {
+  if (b->graph && b->graph_smem == b->smem && b->graph_grid == b->grid) return MPC_OK;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  BCU(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeRelaxed));
+  for (int k = 0; k < b->graph_steps; ++k) {
+    cudaError_t e = launch_step_batch(b->table_dev, b->det, b->grid, b->smem, b->cap_stream);
+    if (e == cudaSuccess) e = launch_advance_batch(b->table_dev, b->adv_grid, b->cap_stream);
+    if (e != cudaSuccess) {
+      cudaStreamEndCapture(b->cap_stream, &g);
+      if (g) cudaGraphDestroy(g);
+      return bfail(b, MPC_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
+  }
+  BCU(b, cudaStreamEndCapture(b->cap_stream, &g));
+  const cudaError_t e = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return bfail(b, MPC_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  b->graph_smem = b->smem;
+  b->graph_grid = b->grid;
+  b->graph_builds += 1;
+  return MPC_OK;
+}
+
+std::string class_key(const mpc_params& p) {
+  char buf[160];
+  std::snprintf(buf, sizeof buf, "v%d n%.6g t%d w%d f%u", p.variant, p.n_c, p.thermostat, p.walls_z,
+                p.flags);
+  return buf;
+}
+
+}  // namespace
+
+extern "C" {
+
+mpc_status mpc_autotune(const mpc_params* p, void* stream, int32_t* tile_particles,
+                        int32_t* threads_per_cell, double* ns_per_particle_step) {
+  if (!p || !tile_particles || !threads_per_cell)
+    return fail(nullptr, MPC_EINVAL, "params and outputs are required");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, MPC_ECUDA, "no CUDA device");
+  }
+  const size_t lim = device_smem_limit(dev);
+  if (lim == 0) return fail(nullptr, MPC_ECUDA, "cannot query shared memory per block");
+  // a cubic box of about 8M particles with p's physics
+  mpc_params q = *p;
+  const int edge = std::max(8, std::min(1024, (int)std::lround(std::cbrt(8.0e6 / std::max(p->n_c, 1e-3)))));
+  q.L[0] = q.L[1] = q.L[2] = edge;
+  q.capacity = 0;
+  q.graph_steps = 8;
+  q.flags &= ~(uint32_t)MPC_FLAG_DEBUG_CELLS;
+  double best = 1e300;
+  int best_tile = 0, best_tpc = 0;
+  for (int tile : {320, 640, 1280}) {
+    Geom g;
+    int64_t N = 0;
+    q.tile_particles = tile;
+    q.threads_per_cell = 0;
+    TRY(plan_box(&q, lim, g, N));
+    const int t0 = g.tpc;
+    for (int tpc : {t0 / 2, t0, t0 * 2, t0 * 4}) {
+      if (tpc < 1 || tpc > 32) continue;
+      const int groups = kStepThreads / tpc;
+      if ((g.brick_cells + groups - 1) / groups > 4) continue;
+      q.threads_per_cell = tpc;
+      mpc_handle h = nullptr;
+      TRY(create_box(&q, static_cast<cudaStream_t>(stream), nullptr, nullptr, &h));
+      double ms = 0.0;
+      int32_t n = 0;
+      mpc_status st = mpc_set_profiling(h, 1);
+      if (st == MPC_OK) st = mpc_step(h, 3);
+      if (st == MPC_OK) st = mpc_synchronize(h);
+      if (st == MPC_OK) st = mpc_step(h, 8);
+      if (st == MPC_OK) st = mpc_synchronize(h);
+      if (st == MPC_OK) st = mpc_profile_step_kernel(h, &ms, &n);
+      const std::string msg = h->err;
+      destroy_box(h, true);
+      if (st != MPC_OK) return fail(nullptr, st, "autotune: " + msg);
+      const double ns = ms * 1e6 / (double)N;
+      if (n > 0 && ns < best) {
+        best = ns;
+        best_tile = tile;
+        best_tpc = tpc;
+      }
+    }
+  }
+  if (best_tile == 0) return fail(nullptr, MPC_ESTATE, "autotune found no candidate");
+  *tile_particles = best_tile;
+  *threads_per_cell = best_tpc;
+  if (ns_per_particle_step) *ns_per_particle_step = best;
+  return MPC_OK;
+}
+
+const char* mpc_batch_last_error(mpc_batch b) {
+  return b ? b->err.c_str() : g_batch_create_error.c_str();
+}
+
+mpc_status mpc_batch_destroy(mpc_batch b) {
+  if (!b) return MPC_OK;
+  cudaSetDevice(b->device);
+  cudaStreamSynchronize(b->stream);
+  for (mpc_handle h : b->boxes) {
+    h->batch = nullptr;
+    destroy_box(h, true);
+  }
+  b->boxes.clear();
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  delete b->arena;
+  if (b->table_dev) cudaFree(b->table_dev);
+  for (int k = 0; k < kTableBuffers; ++k) {
+    if (b->table_host[k]) cudaFreeHost(b->table_host[k]);
+    if (b->table_ev[k]) cudaEventDestroy(b->table_ev[k]);
+  }
+  if (b->ctrl_slab) cudaFreeHost(b->ctrl_slab);
+  if (b->adm_stream) cudaStreamDestroy(b->adm_stream);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  delete b;
+  return MPC_OK;
+}
+
+mpc_status mpc_batch_create(const mpc_batch_config* cfg, void* stream, mpc_batch* out) {
+  if (!out) return bfail(nullptr, MPC_EINVAL, "out is NULL");
+  *out = nullptr;
+  mpc_batch_config c{};
+  if (cfg) c = *cfg;
+  if (c.graph_steps < 0 || c.max_boxes < 0 || c.max_boxes > kMaxBatchBoxes || c.reserved != 0 ||
+      (c.flags & ~(uint32_t)(MPC_BATCH_DETERMINISTIC | MPC_BATCH_AUTOTUNE)))
+    return bfail(nullptr, MPC_EINVAL, "invalid batch configuration");
+  mpc_batch b = new (std::nothrow) mpc_batch_s();
+  if (!b) return bfail(nullptr, MPC_ENOMEM, "host allocation failed");
+  auto bail = [&](mpc_status st, const std::string& msg) {
+    mpc_batch_destroy(b);
+    return bfail(nullptr, st, msg);
+  };
+  if (cudaGetDevice(&b->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return bfail(nullptr, MPC_ECUDA, "no CUDA device");
+  }
+  b->stream = static_cast<cudaStream_t>(stream);
+  b->det = (c.flags & MPC_BATCH_DETERMINISTIC) != 0;
+  b->autotune = (c.flags & MPC_BATCH_AUTOTUNE) != 0;
+  b->graph_steps = c.graph_steps > 0 ? c.graph_steps : 100;
+  b->max_boxes = c.max_boxes > 0 ? c.max_boxes : kMaxBatchBoxes;
+  if (cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess)
+    return bail(MPC_ECUDA, "cannot query the SM count");
+  b->adv_grid = b->num_sms;
+  if (cudaStreamCreateWithFlags(&b->adm_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(MPC_ECUDA, "stream creation failed");
+  if (cudaMallocHost(&b->ctrl_slab, sizeof(Ctrl) * (size_t)b->max_boxes) != cudaSuccess) {
+    b->ctrl_slab = nullptr;
+    return bail(MPC_ENOMEM, "pinned host allocation failed");
+  }
+  for (int k = b->max_boxes - 1; k >= 0; --k) b->free_slots.push_back(k);
+  if (cudaMalloc(&b->table_dev, sizeof(BatchTable)) != cudaSuccess) {
+    b->table_dev = nullptr;
+    return bail(MPC_ENOMEM, "device allocation failed: work table");
+  }
+  for (int k = 0; k < kTableBuffers; ++k) {
+    if (cudaMallocHost(&b->table_host[k], sizeof(BatchTable)) != cudaSuccess) {
+      b->table_host[k] = nullptr;
+      return bail(MPC_ENOMEM, "pinned host allocation failed: work table");
+    }
+    if (cudaEventCreateWithFlags(&b->table_ev[k], cudaEventDisableTiming) != cudaSuccess)
+      return bail(MPC_ECUDA, "event creation failed");
+  }
+  if (c.arena_bytes > 0) {
+    b->arena = new (std::nothrow) Arena();
+    if (!b->arena || !b->arena->init(c.arena_bytes))
+      return bail(MPC_ENOMEM, "device allocation failed: arena");
+    b->alloc.ctx = b->arena;
+    b->alloc.alloc = arena_alloc;
+    b->alloc.release = arena_release;
+  }
+  *out = b;
+  return MPC_OK;
+}
+
+mpc_status mpc_batch_add(mpc_batch b, const mpc_params* p, mpc_handle* out) {
+  if (!b) return bfail(nullptr, MPC_EINVAL, "batch is NULL");
+  if (!p || !out) return bfail(b, MPC_EINVAL, "params and out are required");
+  *out = nullptr;
+  if ((int)b->boxes.size() >= b->max_boxes || b->free_slots.empty())
+    return bfail(b, MPC_EINVAL, "the batch is full");
+  BCU(b, cudaSetDevice(b->device));
+  mpc_params q = *p;
+  if (b->det) q.flags |= MPC_FLAG_DETERMINISTIC;
+  else if (q.flags & MPC_FLAG_DETERMINISTIC)
+    return bfail(b, MPC_EINVAL, "deterministic boxes need a batch created with MPC_BATCH_DETERMINISTIC");
+  if (b->autotune && q.tile_particles == 0 && q.threads_per_cell == 0) {
+    const std::string key = class_key(q);
+    auto it = b->tuned.find(key);
+    if (it == b->tuned.end()) {
+      int32_t tile = 0, tpc = 0;
+      double ns = 0.0;
+      if (mpc_autotune(&q, b->adm_stream, &tile, &tpc, &ns) != MPC_OK)
+        return bfail(b, MPC_ECUDA, std::string("autotune: ") + mpc_last_error(nullptr));
+      it = b->tuned.emplace(key, std::make_pair((int)tile, (int)tpc)).first;
+    }
+    q.tile_particles = it->second.first;
+    q.threads_per_cell = it->second.second;
+  }
+  if (b->arena) {
+    // quick refusal before touching the device: the arena cannot hold the creation peak
+    uint64_t steady = 0, peak = 0;
+    if (mpc_footprint(&q, &steady, &peak) != MPC_OK)
+      return bfail(b, MPC_EINVAL, mpc_last_error(nullptr));
+    b->arena->reclaim(false);
+    if (peak > b->arena->size() - b->arena->used() + b->arena->pending())
+      return bfail(b, MPC_ENOMEM, "the arena cannot hold the box");
+  }
+  const int slot = b->free_slots.back();
+  mpc_handle h = nullptr;
+  const mpc_status st = create_box(&q, b->adm_stream, b->arena ? &b->alloc : nullptr,
+                                   b->ctrl_slab + slot, &h);
+  if (st != MPC_OK) return bfail(b, st, mpc_last_error(nullptr));
+  b->free_slots.pop_back();
+  // the steps enqueued from now on see the created box
+  cudaEvent_t ev = nullptr;
+  BCU(b, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  BCU(b, cudaEventRecord(ev, b->adm_stream));
+  BCU(b, cudaStreamWaitEvent(b->stream, ev, 0));
+  cudaEventDestroy(ev);
+  h->stream = b->stream;
+  h->batch = b;
+  b->slot_of[h] = slot;
+  b->boxes.push_back(h);
+  b->gens.push_back(h->buffers_gen);
+  b->dirty = true;
+  *out = h;
+  return MPC_OK;
+}
+
+mpc_status mpc_batch_remove(mpc_batch b, mpc_handle h) {
+  if (!b) return bfail(nullptr, MPC_EINVAL, "batch is NULL");
+  auto it = std::find(b->boxes.begin(), b->boxes.end(), h);
+  if (!h || it == b->boxes.end()) return bfail(b, MPC_EINVAL, "not a member of this batch");
+  BCU(b, cudaSetDevice(b->device));
+  b->gens.erase(b->gens.begin() + (it - b->boxes.begin()));
+  b->boxes.erase(it);
+  const int slot = b->slot_of[h];
+  b->slot_of.erase(h);
+  h->batch = nullptr;
+  // with an arena, released blocks wait for an event on the batch stream; without one,
+  // wait for the queued steps before cudaFree
+  destroy_box(h, b->arena == nullptr);
+  b->free_slots.push_back(slot);
+  b->dirty = true;
+  return MPC_OK;
+}
+
+mpc_status mpc_batch_step(mpc_batch b, int64_t nsteps) {
+  if (!b) return bfail(nullptr, MPC_EINVAL, "batch is NULL");
+  if (nsteps < 0) return bfail(b, MPC_EINVAL, "nsteps must be >= 0");
+  BCU(b, cudaSetDevice(b->device));
+  if (nsteps == 0 || b->boxes.empty()) return MPC_OK;
+  if (mpc_status st = refresh(b); st != MPC_OK) return st;
+  for (mpc_handle h : b->boxes) h->target_step += std::min(nsteps, h->limit - h->target_step);
+  int64_t n = nsteps;
+  if (n >= b->graph_steps) {
+    if (mpc_status st = build_graph(b); st != MPC_OK) return st;
+    for (; n >= b->graph_steps; n -= b->graph_steps) BCU(b, cudaGraphLaunch(b->graph, b->stream));
+  }
+  for (; n > 0; --n) {
+    BCU(b, launch_step_batch(b->table_dev, b->det, b->grid, b->smem, b->stream));
+    BCU(b, launch_advance_batch(b->table_dev, b->adv_grid, b->stream));
+  }
+  return MPC_OK;
+}
+
+mpc_status mpc_batch_synchronize(mpc_batch b) {
+  if (!b) return bfail(nullptr, MPC_EINVAL, "batch is NULL");
+  BCU(b, cudaSetDevice(b->device));
+  BCU(b, cudaStreamSynchronize(b->stream));
+  mpc_status first = MPC_OK;
+  for (mpc_handle h : b->boxes) {
+    const mpc_status st = sync_and_repair(h);  // refresh() sees reallocated buffers
+    if (st != MPC_OK && first == MPC_OK) {
+      first = st;
+      b->err = "member box: " + h->err;
+    }
+  }
+  return first;
+}
+
+mpc_status mpc_batch_get_info(mpc_batch b, mpc_batch_info* out) {
+  if (!b) return bfail(nullptr, MPC_EINVAL, "batch is NULL");
+  if (!out) return bfail(b, MPC_EINVAL, "out is NULL");
+  std::memset(out, 0, sizeof(*out));
+  int64_t items = 0, parts = 0;
+  for (mpc_handle h : b->boxes) {
+    items += h->g.nbricks;
+    parts += h->N;
+  }
+  out->n_boxes = (int32_t)b->boxes.size();
+  out->work_items = (int32_t)items;
+  out->n_particles = parts;
+  if (b->arena) {
+    b->arena->reclaim(false);
+    out->arena_bytes = b->arena->size();
+    out->arena_used = b->arena->used();
+    out->arena_largest_free = b->arena->largest_free();
+  }
+  out->grid = b->grid;
+  out->ctas_per_sm = b->ctas_per_sm;
+  out->smem_bytes = (int32_t)b->smem;
+  out->graph_builds = b->graph_builds;
+  out->tuned_classes = (int32_t)b->tuned.size();
+  return MPC_OK;
+}
+
+}  // extern "C"

@@ -34,12 +34,14 @@ struct Geom {
   uint32_t key0, key1, box;
   int obs;           // accumulate observables
   int debug;         // keep collision cells and per-cell counts
+  int det;           // fixed-point (order-independent) cell sums and observables
   int64_t ncells;    // Lc[0] Lc[1] Lc[2]
 };
 
 // Device-side control block of a box; written by the step kernels.
 struct Ctrl {
   int64_t step;           // completed steps
+  int64_t limit;          // steps stop (are skipped) once step reaches limit
   int32_t halted;         // a brick overflowed: later steps are skipped until repaired
   int32_t overflow;       // set during the step that overflowed
   int32_t lost;           // the spill area overflowed as well (state unrecoverable)
@@ -48,7 +50,7 @@ struct Ctrl {
   uint32_t pad;
 };
 
-enum : int32_t { kErrBinning = 1, kErrTimeout = 2, kErrRange = 4 };
+enum : int32_t { kErrBinning = 1, kErrTimeout = 2, kErrRange = 4, kErrFixedRange = 8 };
 
 // Particle buffer set: structure of arrays, nbricks * cap entries each.
 struct PBuf {
@@ -84,11 +86,27 @@ struct StepArgs {
   uint32_t* dbg_counts;   // ncells (debug)
 };
 
+// Work table of a batch: box k owns the work items (bricks) [begin[k], begin[k+1]).
+constexpr int kMaxBatchBoxes = 4096;
+struct BatchTable {
+  int32_t nboxes;
+  int32_t total;
+  int32_t begin[kMaxBatchBoxes + 1];
+  StepArgs args[kMaxBatchBoxes];
+};
+
 // launchers (mpc_step.cu)
 size_t step_smem_bytes(const Geom& g);
 cudaError_t configure_step_kernels(const Geom& g);
 cudaError_t launch_step(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_advance(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_store_i64(int64_t* p, int64_t v, cudaStream_t s);
+// batched step: sets the dynamic shared memory of the batched kernel and reports how
+// many of its CTAs fit on one SM
+cudaError_t configure_batch_kernel(bool det, size_t smem_bytes, int* ctas_per_sm);
+cudaError_t launch_step_batch(const BatchTable* t, bool det, int grid, size_t smem_bytes,
+                              cudaStream_t s);
+cudaError_t launch_advance_batch(const BatchTable* t, int grid, cudaStream_t s);
 
 // launchers (mpc_layout.cu)
 cudaError_t launch_init_particles(const Geom& g, int64_t N, uint32_t* const x[3], float* const v[3],

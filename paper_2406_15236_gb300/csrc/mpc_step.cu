@@ -146,10 +146,62 @@ __device__ __forceinline__ int brick_delta(int q, int b, int nb, bool periodic) 
   return (d >= -1 && d <= 1) ? d : 9;
 }
 
-// --- the step kernel ---------------------------------------------------------------
-template <int VAR>
-__global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
-  extern __shared__ __align__(128) unsigned char smem[];
+// Fixed-point cell sums (deterministic mode, Sec. III.B "Reproducibility"): every
+// per-particle term is converted to a 64-bit integer with 32 fraction bits and summed
+// exactly, so a cell's sums do not depend on the order of its members, on the brick
+// geometry or on the number of cooperating threads.  Terms must stay below 2^15 in
+// magnitude (|t| n < 2^31 for the largest admissible cell); larger terms raise
+// kErrFixedRange.  A float32 term above 2^-9 converts without rounding.
+constexpr float kFx = 4294967296.0f;               // 2^32
+constexpr float kUnFx = 2.3283064365386963e-10f;   // 2^-32
+constexpr float kFxLimit = 32768.0f;
+// observables: 24 fraction bits (sums over whole boxes of up to ~2^30 particles)
+constexpr float kObsFx = 16777216.0f;              // 2^24
+constexpr double kObsUnFx = 5.9604644775390625e-08; // 2^-24
+
+__device__ __forceinline__ long long to_fx(float v) { return __float2ll_rn(v * kFx); }
+__device__ __forceinline__ float from_fx(long long s) { return __ll2float_rn(s) * kUnFx; }
+
+__device__ __forceinline__ long long group_sum_fx(long long v, int tpc) {
+  for (int o = tpc >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ long long warp_sum_fx(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// position relative to the cell centre as an integer number of 2^-F units
+__device__ __forceinline__ int rho_int(const Geom& g, uint32_t x, uint32_t s) {
+  return (int)((x + s) & g.mask) - (int)(1u << (g.F - 1));
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Block-wide scalars of one brick's processing (static shared memory).
+struct BrickShared {
+  uint64_t bar;
+  uint32_t cnt, halt;
+  int64_t step;
+  uint32_t gcount[28], gbase[28], gdest[28];
+  union {
+    float f[kThreads / 32][13];
+    long long q[kThreads / 32][13];
+  } obs;
+};
+
+// --- one brick of one box ---------------------------------------------------------
+// Processes brick b of the box described by `a`.  PERSIST: the caller initialised
+// sh.bar once and tracks its phase (persistent kernels); otherwise the barrier is
+// initialised here and phase must be 0.  Returns false after a bounded wait gave up
+// (the CTA must stop).
+template <int VAR, bool DET, bool PERSIST>
+__device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsigned char* smem,
+                                           BrickShared& sh, uint32_t& phase) {
   const Geom& g = a.g;
   const Layout lay = layout_for<VAR>(g);
 
@@ -172,58 +224,57 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
   uint32_t* scstart = reinterpret_cast<uint32_t*>(smem + lay.cstart);
   float* spar = reinterpret_cast<float*>(smem + lay.params);
 
-  __shared__ __align__(8) uint64_t bar;
-  __shared__ uint32_t s_cnt, s_halt;
-  __shared__ int64_t s_step;
-  __shared__ uint32_t gcount[28], gbase[28], gdest[28];
-  __shared__ float s_obs[kThreads / 32][13];
+  uint32_t* gcount = sh.gcount;
+  uint32_t* gbase = sh.gbase;
+  uint32_t* gdest = sh.gdest;
 
   const int tid = threadIdx.x;
   const int lane = tid & 31;
-  const int b = blockIdx.x;
   const int bc = g.brick_cells;
 
-  // ---- 1. load the brick: thread 0 reads the step, the halt flag and both count slots
-  // in one round trip, then starts the bulk copies ----
+  // ---- 1. load the brick: thread 0 reads the step, its limit, the halt flag and both
+  // count slots in one round trip, then starts the bulk copies ----
   if (tid == 0) {
     const int64_t st = *(volatile int64_t*)&a.ctrl->step;
+    const int64_t lim = *(volatile int64_t*)&a.ctrl->limit;
     const int32_t halted = *(volatile int32_t*)&a.ctrl->halted;
     const uint32_t c_even = a.cnt[0][b], c_odd = a.cnt[1][b];
-    s_step = st;
-    s_halt = halted;
+    const bool skip = halted || st >= lim;
+    sh.step = st;
+    sh.halt = skip;
     uint32_t c = 0;
-    if (!halted) {
+    if (!skip) {
       const int p = (int)(st & 1);
       c = p ? c_odd : c_even;
       if (c > (uint32_t)g.cap) c = g.cap;
       a.cnt[p][b] = 0;  // this buffer becomes the destination of the next step
-      mbar_init(&bar, 1);
+      if (!PERSIST) mbar_init(&sh.bar, 1);
       const uint32_t bytes = (uint32_t)(((c + 3) & ~3u) * 4);
-      mbar_expect_tx(&bar, 7u * bytes);
+      mbar_expect_tx(&sh.bar, 7u * bytes);
       if (bytes) {
         const PBuf& sb = a.buf[p];
         const size_t off = (size_t)b * g.cap;
-        bulk_g2s(sx, sb.x[0] + off, bytes, &bar);
-        bulk_g2s(sy, sb.x[1] + off, bytes, &bar);
-        bulk_g2s(sz, sb.x[2] + off, bytes, &bar);
-        bulk_g2s(svx, sb.v[0] + off, bytes, &bar);
-        bulk_g2s(svy, sb.v[1] + off, bytes, &bar);
-        bulk_g2s(svz, sb.v[2] + off, bytes, &bar);
-        bulk_g2s(sid, sb.id + off, bytes, &bar);
+        bulk_g2s(sx, sb.x[0] + off, bytes, &sh.bar);
+        bulk_g2s(sy, sb.x[1] + off, bytes, &sh.bar);
+        bulk_g2s(sz, sb.x[2] + off, bytes, &sh.bar);
+        bulk_g2s(svx, sb.v[0] + off, bytes, &sh.bar);
+        bulk_g2s(svy, sb.v[1] + off, bytes, &sh.bar);
+        bulk_g2s(svz, sb.v[2] + off, bytes, &sh.bar);
+        bulk_g2s(sid, sb.id + off, bytes, &sh.bar);
       }
     }
-    s_cnt = c;
+    sh.cnt = c;
   }
   if (tid < 28) gcount[tid] = 0;
   for (int c = tid; c < bc; c += kThreads) scount[c] = 0;
   __syncthreads();
-  if (s_halt) return;
-  const int64_t step64 = s_step;
+  if (sh.halt) return true;
+  const int64_t step64 = sh.step;
   const uint32_t step = (uint32_t)step64;
   const int par = (int)(step64 & 1);
   const PBuf& dst = a.buf[par ^ 1];
   uint32_t* cnt_dst = a.cnt[par ^ 1];
-  const int cnt = (int)s_cnt;
+  const int cnt = (int)sh.cnt;
   // lattice shifts of this step and the next: one lane per warp draws, the warp shares
   uint3 s0 = make_uint3(0, 0, 0), s1 = make_uint3(0, 0, 0);
   if (lane == 0) {
@@ -234,10 +285,15 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
                  S0z = __shfl_sync(0xffffffffu, s0.z, 0);
   const uint32_t S1x = __shfl_sync(0xffffffffu, s1.x, 0), S1y = __shfl_sync(0xffffffffu, s1.y, 0),
                  S1z = __shfl_sync(0xffffffffu, s1.z, 0);
-  if (!mbar_wait(&bar, 0)) {
-    if (tid == 0) atomicOr(&a.ctrl->errors, kErrTimeout);
-    mbar_wait(&bar, 0);  // give copies in flight one more bounded chance before leaving
-    return;
+  {
+    // every thread waits (bounded); the block leaves together if any wait gave up
+    const bool ok = mbar_wait(&sh.bar, phase);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicOr(&a.ctrl->errors, kErrTimeout);
+      if (!ok) mbar_wait(&sh.bar, phase);  // one more bounded chance for copies in flight
+      return false;
+    }
+    phase ^= 1u;
   }
 
   const int bx = b % g.nb[0];
@@ -316,6 +372,7 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
     const int groups = kThreads / tpc;
     const int grp = tid / tpc, sub = tid & (tpc - 1);
     const int leader = lane & ~(tpc - 1);
+    float fxbig = 0.0f;  // deterministic mode: largest fixed-point term seen by this lane
     for (int c0 = 0; c0 < bc; c0 += groups) {
       const int lc = c0 + grp;
       const int cx = ox + (lc & (g.B[0] - 1));
@@ -328,11 +385,23 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
       if (exists && sub == 0 && g.debug) a.dbg_counts[cg] = (uint32_t)n;
       if constexpr (VAR == 0) {
         float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-        for (int k = sub; k < n; k += tpc) {
-          const int i = sperm[base + k];
-          s0 += svx[i]; s1 += svy[i]; s2 += svz[i];
+        if constexpr (DET) {
+          long long q0 = 0, q1 = 0, q2 = 0;
+          for (int k = sub; k < n; k += tpc) {
+            const int i = sperm[base + k];
+            const float v0 = svx[i], v1 = svy[i], v2 = svz[i];
+            fxbig = fmaxf(fxbig, fmaxf(fabsf(v0), fmaxf(fabsf(v1), fabsf(v2))));
+            q0 += to_fx(v0); q1 += to_fx(v1); q2 += to_fx(v2);
+          }
+          q0 = group_sum_fx(q0, tpc); q1 = group_sum_fx(q1, tpc); q2 = group_sum_fx(q2, tpc);
+          s0 = from_fx(q0); s1 = from_fx(q1); s2 = from_fx(q2);
+        } else {
+          for (int k = sub; k < n; k += tpc) {
+            const int i = sperm[base + k];
+            s0 += svx[i]; s1 += svy[i]; s2 += svz[i];
+          }
+          s0 = group_sum(s0, tpc); s1 = group_sum(s1, tpc); s2 = group_sum(s2, tpc);
         }
-        s0 = group_sum(s0, tpc); s1 = group_sum(s1, tpc); s2 = group_sum(s2, tpc);
         // phantom particles fill the wall part of a cut cell at the mean density
         // (Sec. II, Boundary conditions): Poisson count, Gaussian total momentum, and
         // an internal kinetic energy ~ kT chi^2(3(n_ph - 1)); drawn by the group leader
@@ -364,12 +433,24 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
         if (g.thermostat) {
           // MBS, Eqs. (5)-(7): relative kinetic energy about v_cm (second pass)
           float q = 0.f;
-          for (int k = sub; k < n; k += tpc) {
-            const int i = sperm[base + k];
-            const float dx = svx[i] - vcx, dy = svy[i] - vcy, dz = svz[i] - vcz;
-            q += dx * dx + dy * dy + dz * dz;
+          if constexpr (DET) {
+            long long qq = 0;
+            for (int k = sub; k < n; k += tpc) {
+              const int i = sperm[base + k];
+              const float dx = svx[i] - vcx, dy = svy[i] - vcy, dz = svz[i] - vcz;
+              const float t = dx * dx + dy * dy + dz * dz;
+              fxbig = fmaxf(fxbig, t);
+              qq += to_fx(t);
+            }
+            q = from_fx(group_sum_fx(qq, tpc));
+          } else {
+            for (int k = sub; k < n; k += tpc) {
+              const int i = sperm[base + k];
+              const float dx = svx[i] - vcx, dy = svy[i] - vcy, dz = svz[i] - vcz;
+              q += dx * dx + dy * dy + dz * dz;
+            }
+            q = group_sum(q, tpc);
           }
-          q = group_sum(q, tpc);
           if (exists && n > 0 && sub == 0 && ntot >= 2.0f) {
             float Krel = g.m * q;
             if (nph > 0.0f) {
@@ -396,14 +477,32 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
         // angular-momentum-conserving variants.  First pass: centre of mass and mean of
         // w (AT+a: w = v - v_ran; SRD+a: w = v, so the mean is v_cm)
         float r0 = 0.f, r1 = 0.f, r2 = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f;
-        for (int k = sub; k < n; k += tpc) {
-          const int i = sperm[base + k];
-          r0 += rho_axis(g, sx[i], S0x); r1 += rho_axis(g, sy[i], S0y);
-          r2 += rho_axis(g, sz[i] & ~kCrossedBit, S0z);
-          w0 += svx[i]; w1 += svy[i]; w2 += svz[i];
+        if constexpr (DET) {
+          // positions sum exactly as integers; velocities in fixed point
+          long long R0 = 0, R1 = 0, R2 = 0, W0 = 0, W1 = 0, W2 = 0;
+          for (int k = sub; k < n; k += tpc) {
+            const int i = sperm[base + k];
+            R0 += rho_int(g, sx[i], S0x); R1 += rho_int(g, sy[i], S0y);
+            R2 += rho_int(g, sz[i] & ~kCrossedBit, S0z);
+            const float v0 = svx[i], v1 = svy[i], v2 = svz[i];
+            fxbig = fmaxf(fxbig, fmaxf(fabsf(v0), fmaxf(fabsf(v1), fabsf(v2))));
+            W0 += to_fx(v0); W1 += to_fx(v1); W2 += to_fx(v2);
+          }
+          R0 = group_sum_fx(R0, tpc); R1 = group_sum_fx(R1, tpc); R2 = group_sum_fx(R2, tpc);
+          W0 = group_sum_fx(W0, tpc); W1 = group_sum_fx(W1, tpc); W2 = group_sum_fx(W2, tpc);
+          r0 = __ll2float_rn(R0) * g.inv2F; r1 = __ll2float_rn(R1) * g.inv2F;
+          r2 = __ll2float_rn(R2) * g.inv2F;
+          w0 = from_fx(W0); w1 = from_fx(W1); w2 = from_fx(W2);
+        } else {
+          for (int k = sub; k < n; k += tpc) {
+            const int i = sperm[base + k];
+            r0 += rho_axis(g, sx[i], S0x); r1 += rho_axis(g, sy[i], S0y);
+            r2 += rho_axis(g, sz[i] & ~kCrossedBit, S0z);
+            w0 += svx[i]; w1 += svy[i]; w2 += svz[i];
+          }
+          r0 = group_sum(r0, tpc); r1 = group_sum(r1, tpc); r2 = group_sum(r2, tpc);
+          w0 = group_sum(w0, tpc); w1 = group_sum(w1, tpc); w2 = group_sum(w2, tpc);
         }
-        r0 = group_sum(r0, tpc); r1 = group_sum(r1, tpc); r2 = group_sum(r2, tpc);
-        w0 = group_sum(w0, tpc); w1 = group_sum(w1, tpc); w2 = group_sum(w2, tpc);
         const float inv = 1.0f / fmaxf((float)n, 1.0f);
         const float rcx = r0 * inv, rcy = r1 * inv, rcz = r2 * inv;
         const float wmx = w0 * inv, wmy = w1 * inv, wmz = w2 * inv;
@@ -422,6 +521,7 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
         // collision would change -- AT+a: of w - <w>; SRD+a (Eq. 4): of v_ic - D v_ic
         float Mxx = 0.f, Myy = 0.f, Mzz = 0.f, Mxy = 0.f, Myz = 0.f, Mzx = 0.f;
         float Lx = 0.f, Ly = 0.f, Lz = 0.f;
+        long long qM[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // deterministic mode
         for (int k = sub; k < n; k += tpc) {
           const int i = sperm[base + k];
           const float rx = rho_axis(g, sx[i], S0x) - rcx, ry = rho_axis(g, sy[i], S0y) - rcy,
@@ -435,13 +535,29 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
             const float dz = g.cos_a * wz + g.sin_a * (ax * wy - ay * wx) + t * az;
             wx -= dx; wy -= dy; wz -= dz;
           }
-          Mxx += rx * rx; Myy += ry * ry; Mzz += rz * rz;
-          Mxy += rx * ry; Myz += ry * rz; Mzx += rz * rx;
-          Lx += ry * wz - rz * wy; Ly += rz * wx - rx * wz; Lz += rx * wy - ry * wx;
+          if constexpr (DET) {
+            const float tx = ry * wz - rz * wy, ty = rz * wx - rx * wz, tz = rx * wy - ry * wx;
+            fxbig = fmaxf(fxbig, fmaxf(fabsf(tx), fmaxf(fabsf(ty), fabsf(tz))));
+            qM[0] += to_fx(rx * rx); qM[1] += to_fx(ry * ry); qM[2] += to_fx(rz * rz);
+            qM[3] += to_fx(rx * ry); qM[4] += to_fx(ry * rz); qM[5] += to_fx(rz * rx);
+            qM[6] += to_fx(tx); qM[7] += to_fx(ty); qM[8] += to_fx(tz);
+          } else {
+            Mxx += rx * rx; Myy += ry * ry; Mzz += rz * rz;
+            Mxy += rx * ry; Myz += ry * rz; Mzx += rz * rx;
+            Lx += ry * wz - rz * wy; Ly += rz * wx - rx * wz; Lz += rx * wy - ry * wx;
+          }
         }
-        Mxx = group_sum(Mxx, tpc); Myy = group_sum(Myy, tpc); Mzz = group_sum(Mzz, tpc);
-        Mxy = group_sum(Mxy, tpc); Myz = group_sum(Myz, tpc); Mzx = group_sum(Mzx, tpc);
-        Lx = group_sum(Lx, tpc); Ly = group_sum(Ly, tpc); Lz = group_sum(Lz, tpc);
+        if constexpr (DET) {
+#pragma unroll
+          for (int q = 0; q < 9; ++q) qM[q] = group_sum_fx(qM[q], tpc);
+          Mxx = from_fx(qM[0]); Myy = from_fx(qM[1]); Mzz = from_fx(qM[2]);
+          Mxy = from_fx(qM[3]); Myz = from_fx(qM[4]); Mzx = from_fx(qM[5]);
+          Lx = from_fx(qM[6]); Ly = from_fx(qM[7]); Lz = from_fx(qM[8]);
+        } else {
+          Mxx = group_sum(Mxx, tpc); Myy = group_sum(Myy, tpc); Mzz = group_sum(Mzz, tpc);
+          Mxy = group_sum(Mxy, tpc); Myz = group_sum(Myz, tpc); Mzx = group_sum(Mzx, tpc);
+          Lx = group_sum(Lx, tpc); Ly = group_sum(Ly, tpc); Lz = group_sum(Lz, tpc);
+        }
         if (exists && n > 0 && sub == 0) {
           const float tr = Mxx + Myy + Mzz;
           float ox_ = 0.0f, oy_ = 0.0f, oz_ = 0.0f;
@@ -479,12 +595,18 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
         }
       }
     }
+    if (DET && fxbig >= kFxLimit) atomicOr(&a.ctrl->errors, kErrFixedRange);
   }
   __syncthreads();
 
   // ---- 4. collide, stream for step n+1, count by destination brick ----
   float o_px = 0, o_py = 0, o_pz = 0, o_e = 0, o_kxy = 0, o_kyz = 0, o_kzx = 0;
   float o_c[6] = {0, 0, 0, 0, 0, 0};
+  long long o_q[13];  // deterministic mode: fixed-point observables
+  if constexpr (DET) {
+#pragma unroll
+    for (int q = 0; q < 13; ++q) o_q[q] = 0;
+  }
   const bool zper = !g.walls;
   for (int i = tid; i < cnt; i += kThreads) {
     uint32_t x = sx[i], y = sy[i], z = sz[i] & ~kCrossedBit;
@@ -536,12 +658,20 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
       }
     }
     if (g.obs) {
-      o_px += nx; o_py += ny; o_pz += nz;
-      o_e += nx * nx + ny * ny + nz * nz;
-      o_kxy += vbx * vby; o_kyz += vby * vbz; o_kzx += vbz * vbx;
-      const float dx = nx - vbx, dy = ny - vby, dz = nz - vbz;
-      o_c[0] += dx * py; o_c[1] += dy * px; o_c[2] += dy * pz;
-      o_c[3] += dz * py; o_c[4] += dz * px; o_c[5] += dx * pz;
+      if constexpr (DET) {
+        const float dx = nx - vbx, dy = ny - vby, dz = nz - vbz;
+        const float t[13] = {nx, ny, nz, nx * nx + ny * ny + nz * nz, vbx * vby, vby * vbz,
+                             vbz * vbx, dx * py, dy * px, dy * pz, dz * py, dz * px, dx * pz};
+#pragma unroll
+        for (int q = 0; q < 13; ++q) o_q[q] += __float2ll_rn(t[q] * kObsFx);
+      } else {
+        o_px += nx; o_py += ny; o_pz += nz;
+        o_e += nx * nx + ny * ny + nz * nz;
+        o_kxy += vbx * vby; o_kyz += vby * vbz; o_kzx += vbz * vbx;
+        const float dx = nx - vbx, dy = ny - vby, dz = nz - vbz;
+        o_c[0] += dx * py; o_c[1] += dy * px; o_c[2] += dy * pz;
+        o_c[3] += dz * py; o_c[4] += dz * px; o_c[5] += dx * pz;
+      }
     }
     // stream for step n+1 (this is the only streaming of the particle per step) and
     // find the brick of its next collision cell
@@ -577,11 +707,19 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
   }
   if (g.obs) {
     const int w = tid >> 5;
-    float vals[13] = {o_px, o_py, o_pz, o_e, o_kxy, o_kyz, o_kzx, o_c[0], o_c[1], o_c[2], o_c[3], o_c[4], o_c[5]};
+    if constexpr (DET) {
 #pragma unroll
-    for (int q = 0; q < 13; ++q) {
-      const float s = warp_sum(vals[q]);
-      if (lane == 0) s_obs[w][q] = s;
+      for (int q = 0; q < 13; ++q) {
+        const long long s = warp_sum_fx(o_q[q]);
+        if (lane == 0) sh.obs.q[w][q] = s;
+      }
+    } else {
+      float vals[13] = {o_px, o_py, o_pz, o_e, o_kxy, o_kyz, o_kzx, o_c[0], o_c[1], o_c[2], o_c[3], o_c[4], o_c[5]};
+#pragma unroll
+      for (int q = 0; q < 13; ++q) {
+        const float s = warp_sum(vals[q]);
+        if (lane == 0) sh.obs.f[w][q] = s;
+      }
     }
   }
   __syncthreads();
@@ -599,9 +737,17 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
   }
   if (g.obs && tid >= 32 && tid < 32 + 13) {
     const int q = tid - 32;
-    double s = 0.0;
-    for (int w = 0; w < kThreads / 32; ++w) s += (double)s_obs[w][q];
-    atomicAdd(&a.obs_partials[(b % kObsSlots) * kObsWidth + q], s);
+    double* slot = &a.obs_partials[(b % kObsSlots) * kObsWidth + q];
+    if constexpr (DET) {
+      // integer partials: the order of the atomics does not matter
+      long long s = 0;
+      for (int w = 0; w < kThreads / 32; ++w) s += sh.obs.q[w][q];
+      atomicAdd(reinterpret_cast<unsigned long long*>(slot), (unsigned long long)s);
+    } else {
+      double s = 0.0;
+      for (int w = 0; w < kThreads / 32; ++w) s += (double)sh.obs.f[w][q];
+      atomicAdd(slot, s);
+    }
   }
   __syncthreads();
 
@@ -640,24 +786,83 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
       }
     }
   }
+  return true;
 }
 
-// Closes a step: reduces the observables partials into the ring, advances the step
-// counter and stops the chain after an overflow.  One block of kObsSlots threads.
-__global__ void k_advance(const StepArgs a) {
-  __shared__ int32_t s_halt;
+// --- kernels -------------------------------------------------------------------------
+
+// One box: one CTA per brick.
+template <int VAR, bool DET>
+__global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ BrickShared sh;
+  uint32_t phase = 0;
+  step_brick<VAR, DET, false>(a, blockIdx.x, smem, sh, phase);
+}
+
+// Many boxes of any variant in one persistent launch: the CTAs stride over the packed
+// list of (box, brick) work items; box k owns items [begin[k], begin[k+1]).
+template <bool DET>
+__global__ void __launch_bounds__(kThreads, 5) k_step_batch(const BatchTable* __restrict__ t) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ BrickShared sh;
+  __shared__ int s_box;
+  if (threadIdx.x == 0) mbar_init(&sh.bar, 1);
+  __syncthreads();
+  uint32_t phase = 0;
+  const int total = t->total;
+  const int nboxes = t->nboxes;
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    if (threadIdx.x == 0) {
+      int lo = 0, hi = nboxes - 1;  // last box whose first item is <= w
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (t->begin[mid] <= w) lo = mid;
+        else hi = mid - 1;
+      }
+      s_box = lo;
+    }
+    __syncthreads();
+    const int k = s_box;
+    const StepArgs& a = t->args[k];
+    const int b = w - t->begin[k];
+    bool ok;
+    if (a.g.variant == 0) ok = step_brick<0, DET, true>(a, b, smem, sh, phase);
+    else if (a.g.variant == 1) ok = step_brick<1, DET, true>(a, b, smem, sh, phase);
+    else ok = step_brick<2, DET, true>(a, b, smem, sh, phase);
+    if (!ok) return;
+    // the next item's bulk copies overwrite shared memory this item wrote
+    fence_proxy_async_smem();
+    __syncthreads();
+  }
+}
+
+// Closes a step of one box: reduces the observables partials into the ring, advances
+// the step counter (up to its limit) and stops the chain after an overflow.  Runs on one
+// block of kObsSlots threads.
+__device__ __forceinline__ void advance_box(const StepArgs& a) {
+  __shared__ int32_t s_skip;
   __shared__ int64_t s_step;
   if (threadIdx.x == 0) {
-    s_halt = *(volatile int32_t*)&a.ctrl->halted;
-    s_step = *(volatile int64_t*)&a.ctrl->step;
+    const int64_t st = *(volatile int64_t*)&a.ctrl->step;
+    const int64_t lim = *(volatile int64_t*)&a.ctrl->limit;
+    s_skip = *(volatile int32_t*)&a.ctrl->halted || st >= lim;
+    s_step = st;
   }
   __syncthreads();
-  if (s_halt) return;
+  if (s_skip) return;
   if (a.g.obs) {
     const int q = threadIdx.x;
     if (q < kObsWidth) {
       double s = 0.0;
-      for (int k = 0; k < kObsSlots; ++k) s += a.obs_partials[k * kObsWidth + q];
+      if (a.g.det) {
+        long long t = 0;
+        for (int k = 0; k < kObsSlots; ++k)
+          t += reinterpret_cast<const long long*>(a.obs_partials)[k * kObsWidth + q];
+        s = (double)t * kObsUnFx;
+      } else {
+        for (int k = 0; k < kObsSlots; ++k) s += a.obs_partials[k * kObsWidth + q];
+      }
       double* row = a.obs_series + (size_t)(s_step % a.obs_ring) * kObsWidth;
       row[q] = (q == 13) ? (double)(s_step + 1) : s;
     }
@@ -670,37 +875,92 @@ __global__ void k_advance(const StepArgs a) {
   }
 }
 
+__global__ void k_advance(const StepArgs a) { advance_box(a); }
+
+__global__ void k_advance_batch(const BatchTable* __restrict__ t) {
+  const int nboxes = t->nboxes;
+  for (int k = blockIdx.x; k < nboxes; k += gridDim.x) {
+    advance_box(t->args[k]);
+    __syncthreads();
+  }
+}
+
+// stores v at p (a step limit) in stream order
+__global__ void k_store_i64(int64_t* p, int64_t v) { *p = v; }
+
 size_t step_smem_bytes(const Geom& g) {
   if (g.variant == 0) return layout_for<0>(g).total;
   if (g.variant == 1) return layout_for<1>(g).total;
   return layout_for<2>(g).total;
 }
 
+template <bool DET>
+cudaError_t set_step_smem(const Geom& g, size_t bytes) {
+  cudaError_t e;
+  if (g.variant == 0)
+    e = cudaFuncSetAttribute(k_step<0, DET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  else if (g.variant == 1)
+    e = cudaFuncSetAttribute(k_step<1, DET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  else
+    e = cudaFuncSetAttribute(k_step<2, DET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return e;
+}
+
 cudaError_t configure_step_kernels(const Geom& g) {
   const size_t bytes = step_smem_bytes(g);
-  cudaError_t e = cudaSuccess;
-  if (g.variant == 0)
-    e = cudaFuncSetAttribute(k_step<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  else if (g.variant == 1)
-    e = cudaFuncSetAttribute(k_step<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return g.det ? set_step_smem<true>(g, bytes) : set_step_smem<false>(g, bytes);
+}
+
+template <bool DET>
+void launch_step_t(const StepArgs& a, size_t bytes, cudaStream_t s) {
+  if (a.g.variant == 0)
+    k_step<0, DET><<<a.g.nbricks, kThreads, bytes, s>>>(a);
+  else if (a.g.variant == 1)
+    k_step<1, DET><<<a.g.nbricks, kThreads, bytes, s>>>(a);
   else
-    e = cudaFuncSetAttribute(k_step<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  return e;
+    k_step<2, DET><<<a.g.nbricks, kThreads, bytes, s>>>(a);
 }
 
 cudaError_t launch_step(const StepArgs& a, cudaStream_t s) {
   const size_t bytes = step_smem_bytes(a.g);
-  if (a.g.variant == 0)
-    k_step<0><<<a.g.nbricks, kThreads, bytes, s>>>(a);
-  else if (a.g.variant == 1)
-    k_step<1><<<a.g.nbricks, kThreads, bytes, s>>>(a);
-  else
-    k_step<2><<<a.g.nbricks, kThreads, bytes, s>>>(a);
+  if (a.g.det) launch_step_t<true>(a, bytes, s);
+  else launch_step_t<false>(a, bytes, s);
   return cudaGetLastError();
 }
 
 cudaError_t launch_advance(const StepArgs& a, cudaStream_t s) {
   k_advance<<<1, kObsSlots, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_store_i64(int64_t* p, int64_t v, cudaStream_t s) {
+  k_store_i64<<<1, 1, 0, s>>>(p, v);
+  return cudaGetLastError();
+}
+
+cudaError_t configure_batch_kernel(bool det, size_t smem_bytes, int* ctas_per_sm) {
+  cudaError_t e;
+  if (det) {
+    e = cudaFuncSetAttribute(k_step_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_step_batch<true>, kThreads, smem_bytes);
+  } else {
+    e = cudaFuncSetAttribute(k_step_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_step_batch<false>, kThreads, smem_bytes);
+  }
+  return e;
+}
+
+cudaError_t launch_step_batch(const BatchTable* t, bool det, int grid, size_t smem_bytes,
+                              cudaStream_t s) {
+  if (det) k_step_batch<true><<<grid, kThreads, smem_bytes, s>>>(t);
+  else k_step_batch<false><<<grid, kThreads, smem_bytes, s>>>(t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance_batch(const BatchTable* t, int grid, cudaStream_t s) {
+  k_advance_batch<<<grid, kObsSlots, 0, s>>>(t);
   return cudaGetLastError();
 }
 

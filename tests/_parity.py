@@ -29,7 +29,8 @@ def oracle_params(**kw):
     m = dict(kw)
     variant = m.pop("variant", 0)
     g = m.pop("gravity", (0.0, 0.0, 0.0))
-    for k in ("flags", "capacity", "graph_steps", "box_id"):
+    for k in ("flags", "capacity", "graph_steps", "box_id", "tile_particles", "threads_per_cell",
+              "obs_ring"):
         m.pop(k, None)
     return oracle.params(variant=variant, g=g, **m)
 

@@ -34,26 +34,44 @@ def test_version_and_error_text():
     assert "sm_103a" in mpc.mpc_version()
 
 
+LAYOUT = [
+    ("sizeof(mpc_params)", lambda: ctypes.sizeof(mpc.mpc_params)),
+    ("sizeof(mpc_allocator)", lambda: ctypes.sizeof(mpc.mpc_allocator)),
+    ("sizeof(mpc_obs)", lambda: ctypes.sizeof(mpc.mpc_obs)),
+    ("sizeof(mpc_info)", lambda: ctypes.sizeof(mpc.mpc_info)),
+    ("sizeof(mpc_batch_config)", lambda: ctypes.sizeof(mpc.mpc_batch_config)),
+    ("sizeof(mpc_batch_info)", lambda: ctypes.sizeof(mpc.mpc_batch_info)),
+    ("offsetof(mpc_params, seed)", lambda: mpc.mpc_params.seed.offset),
+    ("offsetof(mpc_params, graph_steps)", lambda: mpc.mpc_params.graph_steps.offset),
+    ("offsetof(mpc_params, tile_particles)", lambda: mpc.mpc_params.tile_particles.offset),
+    ("offsetof(mpc_params, obs_ring)", lambda: mpc.mpc_params.obs_ring.offset),
+    ("offsetof(mpc_obs, step)", lambda: mpc.mpc_obs.step.offset),
+    ("offsetof(mpc_info, threads_per_cell)", lambda: mpc.mpc_info.threads_per_cell.offset),
+    ("offsetof(mpc_batch_config, flags)", lambda: mpc.mpc_batch_config.flags.offset),
+    ("offsetof(mpc_batch_info, grid)", lambda: mpc.mpc_batch_info.grid.offset),
+    ("offsetof(mpc_batch_info, tuned_classes)", lambda: mpc.mpc_batch_info.tuned_classes.offset),
+]
+
+
 def test_struct_layouts_match_header(tmp_path):
     src = tmp_path / "sz.c"
+    body = "".join(f'printf("%zu\\n", (size_t){expr});' for expr, _ in LAYOUT)
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "mpc.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(mpc_params),'
-                   ' sizeof(mpc_allocator), sizeof(mpc_obs), sizeof(mpc_info),'
-                   ' offsetof(mpc_params, seed), offsetof(mpc_params, graph_steps),'
-                   ' offsetof(mpc_obs, step));return 0;}\n')
+                   'int main(void){' + body + 'return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
-    want = [ctypes.sizeof(mpc.mpc_params), ctypes.sizeof(mpc.mpc_allocator),
-            ctypes.sizeof(mpc.mpc_obs), ctypes.sizeof(mpc.mpc_info),
-            mpc.mpc_params.seed.offset, mpc.mpc_params.graph_steps.offset, mpc.mpc_obs.step.offset]
-    assert got == want
+    want = [f() for _, f in LAYOUT]
+    assert got == want, list(zip([e for e, _ in LAYOUT], got, want))
 
 
 @pytest.mark.parametrize("bad", [dict(L=1), dict(L=(8, 8, 2000)), dict(h=0.0), dict(kT=-1.0),
                                  dict(n_c=0.0), dict(variant=7), dict(variant=1, thermostat=1),
                                  dict(variant=1, walls_z=1), dict(capacity=-3),
-                                 dict(gravity=(float("nan"), 0.0, 0.0))])
+                                 dict(gravity=(float("nan"), 0.0, 0.0)),
+                                 dict(tile_particles=-1), dict(tile_particles=20000),
+                                 dict(threads_per_cell=3), dict(threads_per_cell=64),
+                                 dict(obs_ring=-1), dict(flags=64)])
 def test_invalid_parameters_rejected_without_device(bad):
     p = mpc.make_params(**bad)
     with pytest.raises(mpc.MpcError) as e:
@@ -75,3 +93,29 @@ def test_null_handle_calls_fail_cleanly():
     assert lib.mpc_step(None, 1) == mpc.MPC_EINVAL
     assert lib.mpc_synchronize(None) == mpc.MPC_EINVAL
     assert lib.mpc_destroy(None) == mpc.MPC_OK
+
+
+def test_reserved_field_must_be_zero():
+    p = mpc.make_params()
+    p.reserved = 1
+    with pytest.raises(mpc.MpcError) as e:
+        mpc.mpc_create(p)
+    assert e.value.status == mpc.MPC_EINVAL
+
+
+def test_null_batch_calls_fail_cleanly():
+    lib = mpc.lib()
+    assert lib.mpc_batch_step(None, 1) == mpc.MPC_EINVAL
+    assert lib.mpc_batch_synchronize(None) == mpc.MPC_EINVAL
+    assert lib.mpc_batch_remove(None, None) == mpc.MPC_EINVAL
+    assert lib.mpc_batch_destroy(None) == mpc.MPC_OK
+    assert lib.mpc_set_step_limit(None, 5) == mpc.MPC_EINVAL
+
+
+def test_invalid_batch_config_rejected_without_device():
+    cfg = mpc.mpc_batch_config()
+    cfg.max_boxes = 100000
+    with pytest.raises(mpc.MpcError) as e:
+        mpc.mpc_batch_create(cfg)
+    assert e.value.status == mpc.MPC_EINVAL
+    assert mpc.mpc_batch_last_error()
