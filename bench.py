@@ -56,6 +56,10 @@ def parse_args(argv=None):
     ap.add_argument("--no-observables", action="store_true",
                     help="do not accumulate observables inside the step (they are then "
                          "reduced from the state when read)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-ensemble leg")
+    ap.add_argument("--batch-boxes", type=int, default=256)
+    ap.add_argument("--batch-steps", type=int, default=100)
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     return ap.parse_args(argv)
 
 
@@ -256,6 +260,91 @@ def run_reference(args):
     return 0
 
 
+# --- batched ensemble --------------------------------------------------------------------------------
+
+BATCH_KINDS = (("SRD", 90.0), ("SRD", 130.0), ("AT+a", 130.0))
+
+
+def ensemble(n: int, seed: int = 4):
+    """The batched workload: n periodic boxes, L uniform in {8, 12, ..., 64}, N_c in
+    {5, 10, 20}, variant SRD 90 deg / SRD 130 deg / AT+a, h in {0.02, 0.05, 0.1},
+    Philox seeds 1000 + b (box_id b)."""
+    import numpy as np
+
+    rng = np.random.default_rng(seed)
+    Ls = rng.choice(np.arange(8, 65, 4), n)
+    ncs = rng.choice([5.0, 10.0, 20.0], n)
+    kinds = rng.integers(0, len(BATCH_KINDS), n)
+    hs = rng.choice([0.02, 0.05, 0.1], n)
+    out = []
+    for b in range(n):
+        name, alpha = BATCH_KINDS[int(kinds[b])]
+        out.append(dict(L=int(Ls[b]), n_c=float(ncs[b]), h=float(hs[b]), alpha_deg=alpha,
+                        variant=1 if name == "AT+a" else 0, seed=1000 + b, box_id=b))
+    return out
+
+
+def run_batched(args, mpc, torch) -> dict:
+    """All boxes in one batch (small boxes packed by variant into persistent launches,
+    large ones in their own launches, graphs of K steps, tiles picked by the autotuner)
+    against the same boxes stepped one at a time with the plain single-box path (one
+    box's K-step graph after another), same arithmetic."""
+    boxes = ensemble(args.batch_boxes)
+    K = args.batch_steps
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    batch = mpc.Batch(graph_steps=K, autotune=True)
+    members = [batch.add(**kw) for kw in boxes]
+    t_setup = time.perf_counter() - t0
+    total_n = sum(m.N for m in members)
+    batch.step(K)  # warm-up: one graph of K steps
+    batch.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    batch.step(K)
+    e1.record(stream)
+    batch.synchronize()
+    ms_batch = e0.elapsed_time(e1)
+    info = batch.info()
+    steps_ok = all(m.get_state()[3] == 2 * K for m in members[:4])
+    batch.close()
+
+    sims = [mpc.Simulation(graph_steps=K, **kw) for kw in boxes]
+    for s_ in sims:
+        s_.step(3)
+    for s_ in sims:
+        s_.synchronize()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for s_ in sims:
+        s_.step(K)
+    e1.record(stream)
+    for s_ in sims:
+        s_.synchronize()
+    ms_plain = e0.elapsed_time(e1)
+    for s_ in sims:
+        s_.close()
+    jobs_steps = 10000
+    return {
+        "workload": f"{len(boxes)} periodic boxes, L in {{8,12,...,64}}, N_c in {{5,10,20}}, "
+                    "SRD 90/130 deg or AT+a, h in {0.02,0.05,0.1}, seeds 1000+b",
+        "boxes": len(boxes), "particles": total_n, "steps_timed": K,
+        "ms_per_step": ms_batch / K, "particle_steps_per_s": total_n * K / (ms_batch / 1e3),
+        "jobs_per_s": len(boxes) / (ms_batch / 1e3 * jobs_steps / K),
+        "plain_ms_per_step": ms_plain / K,
+        "plain_particle_steps_per_s": total_n * K / (ms_plain / 1e3),
+        "plain_jobs_per_s": len(boxes) / (ms_plain / 1e3 * jobs_steps / K),
+        "speedup_vs_plain": ms_plain / ms_batch,
+        "job": f"{jobs_steps} steps per box (jobs/s extrapolated from the timed steps)",
+        "grid": info.grid, "ctas_per_sm": info.ctas_per_sm, "smem_bytes": info.smem_bytes,
+        "work_items": info.work_items, "tuned_classes": info.tuned_classes,
+        "solo_boxes": info.solo_boxes, "packed_launches": info.packed_launches,
+        "setup_s_incl_autotune": t_setup,
+        "gpu_launches_per_step": info.solo_boxes + info.packed_launches + 1,
+        "steps_check": steps_ok}
+
+
 # --- our arm ----------------------------------------------------------------------------------------
 
 def run_ours(args):
@@ -356,6 +445,11 @@ def run_ours(args):
                 "bytes_per_particle": BYTES_PER_PARTICLE, "peak_source": peak_src + ", of measured",
                 "frac_two_sweep_72B_model": value / world * TWO_SWEEP_MODEL_BYTES / 1e9 / peak}
 
+    sim.close()
+    batched = None
+    if rank == 0 and world == 1 and not args.no_batch:
+        batched = run_batched(args, mpc, torch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, cores, sample = cpu_oracle_rate(args, budget=args.cpu_seconds, L=32)
@@ -369,9 +463,9 @@ def run_ours(args):
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
                 "clocks": clk,
                 "checks": {"momentum": [float(x) for x in obs["momentum"]],
-                           "temperature": obs["temperature"], "step": obs["step"]}}
+                           "temperature": obs["temperature"], "step": obs["step"]},
+                "batched": batched}
         print(json.dumps(line), flush=True)
-    sim.close()
     if world > 1:
         import torch.distributed as dist
 

@@ -219,19 +219,23 @@ mpc_status mpc_set_step_limit(mpc_handle h, int64_t limit);
 mpc_status mpc_footprint(const mpc_params* p, uint64_t* steady_bytes, uint64_t* peak_bytes);
 
 /* Picks tile_particles and threads_per_cell for boxes like p by timing the fused step
- * kernel on a box with p's parameters (edges clipped so it holds about 8M particles):
- * tiles of about 320, 640 and 1280 particles, each with the thread splits that finalise
- * a brick in at most four passes.  Results are written to *tile_particles,
- * *threads_per_cell and *ns_per_particle_step (the best time); the parameters chosen
- * change only speed (with MPC_FLAG_DETERMINISTIC not even the rounding).  Allocates
- * and frees device memory with cudaMalloc; synchronises `stream`. */
-mpc_status mpc_autotune(const mpc_params* p, void* stream, int32_t* tile_particles,
-                        int32_t* threads_per_cell, double* ns_per_particle_step);
+ * kernel on a cubic box with p's physics and about 8M particles: tiles of about 320,
+ * 640 and 1280 particles whose shared memory per CTA stays within max_smem_bytes (0: no
+ * bound), each with the thread splits that finalise a brick in at most four passes.
+ * Results are written to *tile_particles, *threads_per_cell and *ns_per_particle_step
+ * (the best time); the parameters chosen change only speed (with
+ * MPC_FLAG_DETERMINISTIC not even the rounding).  Allocates and frees device memory
+ * with cudaMalloc; synchronises `stream`. */
+mpc_status mpc_autotune(const mpc_params* p, void* stream, uint64_t max_smem_bytes,
+                        int32_t* tile_particles, int32_t* threads_per_cell,
+                        double* ns_per_particle_step);
 
 /* ---- Batches: many independent boxes advanced together ----------------------------
- * The paper runs one system per job; a batch packs many boxes (any L, variant, alpha,
- * h, n_c, seed) into one persistent launch of the fused step per time step, over the
- * concatenated list of every box's bricks, inside CUDA graphs of graph_steps steps.
+ * The paper runs one system per job; a batch advances many boxes (any L, variant,
+ * alpha, h, n_c, seed) together, inside CUDA graphs of graph_steps steps.  Per step,
+ * small boxes are packed by variant into persistent launches (up to 48 boxes each, the
+ * CTAs claiming the boxes' bricks from one work list); boxes with at least two GPU
+ * waves of bricks get their own single-box launch in the same step.
  * Member boxes are ordinary handles (mpc_get_state, mpc_observables, ... work on them)
  * created and destroyed through the batch; their device memory comes from the batch's
  * arena when it has one.  A batch and its members are used by one host thread. */
@@ -239,9 +243,12 @@ typedef struct mpc_batch_s* mpc_batch;
 
 enum {
   MPC_BATCH_DETERMINISTIC = 1u,  /* members get MPC_FLAG_DETERMINISTIC */
-  MPC_BATCH_AUTOTUNE = 2u        /* members without explicit tile_particles /
+  MPC_BATCH_AUTOTUNE = 2u,       /* members without explicit tile_particles /
                                     threads_per_cell are tuned per class (variant,
                                     n_c, thermostat, walls, flags) with mpc_autotune */
+  MPC_BATCH_PACK_ALL = 4u        /* pack every member, whatever its size; by default
+                                    members with at least two GPU waves of bricks
+                                    (2 x 5 x SMs) get their own single-box launch */
 };
 
 typedef struct {
@@ -256,14 +263,16 @@ typedef struct {
 
 typedef struct {
   int32_t n_boxes;
-  int32_t work_items;       /* bricks over all members */
+  int32_t work_items;       /* bricks of the packed members */
   int64_t n_particles;
   uint64_t arena_bytes, arena_used, arena_largest_free;
-  int32_t grid;             /* CTAs of the persistent step launch */
-  int32_t ctas_per_sm;
-  int32_t smem_bytes;       /* dynamic shared memory per CTA (largest member) */
+  int32_t grid;             /* CTAs of the packed launches of one step, summed */
+  int32_t ctas_per_sm;      /* largest occupancy of a packed launch */
+  int32_t smem_bytes;       /* largest dynamic shared memory per CTA of a packed launch */
   int32_t graph_builds;
   int32_t tuned_classes;
+  int32_t solo_boxes;       /* members stepped by their own single-box launch */
+  int32_t packed_launches;  /* persistent launches per step for the packed members */
   int32_t reserved;
 } mpc_batch_info;
 

@@ -22,7 +22,7 @@ _LIB_PATH = _build.LIB
 MPC_SRD, MPC_AT_A, MPC_SRD_A = 0, 1, 2
 MPC_OK, MPC_EINVAL, MPC_ENOMEM, MPC_ECUDA, MPC_ETIMEOUT, MPC_ESTATE = range(6)
 MPC_FLAG_OBSERVABLES, MPC_FLAG_DEBUG_CELLS, MPC_FLAG_DETERMINISTIC = 1, 2, 4
-MPC_BATCH_DETERMINISTIC, MPC_BATCH_AUTOTUNE = 1, 2
+MPC_BATCH_DETERMINISTIC, MPC_BATCH_AUTOTUNE, MPC_BATCH_PACK_ALL = 1, 2, 4
 STATUS_NAMES = {0: "MPC_OK", 1: "MPC_EINVAL", 2: "MPC_ENOMEM", 3: "MPC_ECUDA",
                 4: "MPC_ETIMEOUT", 5: "MPC_ESTATE"}
 OBS_ROW = ["px", "py", "pz", "sum_v2", "skin_xy", "skin_yz", "skin_zx", "scol_xy", "scol_yx",
@@ -84,7 +84,8 @@ class mpc_batch_info(ctypes.Structure):
                 ("arena_used", ctypes.c_uint64), ("arena_largest_free", ctypes.c_uint64),
                 ("grid", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("smem_bytes", ctypes.c_int32), ("graph_builds", ctypes.c_int32),
-                ("tuned_classes", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("tuned_classes", ctypes.c_int32), ("solo_boxes", ctypes.c_int32),
+                ("packed_launches", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -120,8 +121,8 @@ def lib():
                                            vp, vp]
     L.mpc_set_step_limit.argtypes = [vp, ctypes.c_int64]
     L.mpc_footprint.argtypes = [P(mpc_params), P(ctypes.c_uint64), P(ctypes.c_uint64)]
-    L.mpc_autotune.argtypes = [P(mpc_params), vp, P(ctypes.c_int32), P(ctypes.c_int32),
-                               P(ctypes.c_double)]
+    L.mpc_autotune.argtypes = [P(mpc_params), vp, ctypes.c_uint64, P(ctypes.c_int32),
+                               P(ctypes.c_int32), P(ctypes.c_double)]
     L.mpc_batch_create.argtypes = [P(mpc_batch_config), vp, P(vp)]
     L.mpc_batch_destroy.argtypes = [vp]
     L.mpc_batch_add.argtypes = [vp, P(mpc_params), P(vp)]
@@ -308,11 +309,12 @@ def mpc_footprint(params: mpc_params):
     return s.value, p.value
 
 
-def mpc_autotune(params: mpc_params, stream=None):
+def mpc_autotune(params: mpc_params, stream=None, max_smem_bytes=0):
     """(tile_particles, threads_per_cell, ns per particle-step) picked by timing."""
     t, c, ns = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
-    _check(lib().mpc_autotune(ctypes.byref(params), ctypes.c_void_p(stream or 0), ctypes.byref(t),
-                              ctypes.byref(c), ctypes.byref(ns)))
+    _check(lib().mpc_autotune(ctypes.byref(params), ctypes.c_void_p(stream or 0),
+                              int(max_smem_bytes), ctypes.byref(t), ctypes.byref(c),
+                              ctypes.byref(ns)))
     return t.value, c.value, ns.value
 
 
@@ -443,17 +445,18 @@ class Simulation(Box):
 
 
 class Batch:
-    """Many independent boxes advanced together by one persistent launch per step."""
+    """Many independent boxes advanced together: small boxes packed by variant into
+    persistent launches, large ones in their own launches, one CUDA graph per chunk."""
 
     def __init__(self, arena_bytes=0, graph_steps=0, deterministic=False, autotune=False,
-                 max_boxes=0, stream=None):
+                 max_boxes=0, stream=None, pack_all=False):
         import torch
 
         cfg = mpc_batch_config()
         cfg.arena_bytes = int(arena_bytes)
         cfg.graph_steps = int(graph_steps)
         cfg.flags = (MPC_BATCH_DETERMINISTIC if deterministic else 0) | \
-            (MPC_BATCH_AUTOTUNE if autotune else 0)
+            (MPC_BATCH_AUTOTUNE if autotune else 0) | (MPC_BATCH_PACK_ALL if pack_all else 0)
         cfg.max_boxes = int(max_boxes)
         cfg.reserved = 0
         if stream is None:

@@ -263,7 +263,7 @@ mpc_status bin_into_bricks(mpc_handle h, const PBuf& src, int64_t n, int64_t ste
     free_particle_buffers(h);
     g.cap = want;
     TRY(alloc_particle_buffers(h));
-    CU(h, configure_step_kernels(g));
+    CU(h, configure_step_kernels(h->smem_limit));
     if (h->graph) {
       cudaGraphExecDestroy(h->graph);
       h->graph = nullptr;
@@ -403,7 +403,7 @@ mpc_status repair_overflow(mpc_handle h) {
   free_particle_buffers(h);
   g.cap = trial.cap;
   TRY(alloc_particle_buffers(h));
-  CU(h, configure_step_kernels(g));
+  CU(h, configure_step_kernels(h->smem_limit));
   if (h->graph) {
     cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
@@ -575,7 +575,7 @@ mpc_status create_box(const mpc_params* p, cudaStream_t stream, const mpc_alloca
   if ((st = alloc_array(h, &h->obs_series, (size_t)h->obs_ring * kObsWidth, "observables")) != MPC_OK) return bail(st);
   if (g.debug && (st = alloc_array(h, &h->dbg_counts, (size_t)g.ncells, "debug counts")) != MPC_OK) return bail(st);
   if ((st = alloc_particle_buffers(h)) != MPC_OK) return bail(st);
-  if (configure_step_kernels(g) != cudaSuccess)
+  if (configure_step_kernels(h->smem_limit) != cudaSuccess)
     return bail(fail(h, MPC_ECUDA, "cannot configure the step kernel (shared memory)"));
   if (cudaMemsetAsync(h->obs_series, 0, sizeof(double) * h->obs_ring * kObsWidth, h->stream) != cudaSuccess)
     return bail(fail(h, MPC_ECUDA, "memset"));

@@ -1,12 +1,15 @@
 // Batches of independent MPC boxes (C ABI in include/mpc.h) and the kernel autotuner.
 //
-// A batch keeps a device work table (BatchTable): the step arguments of every member
-// and the prefix of their brick counts.  One persistent launch of the fused step kernel
-// per time step strides over all members' bricks; a second small launch closes the step
-// of every member.  Both are captured in a CUDA graph of graph_steps steps that reads
-// the table through a fixed pointer, so adding or removing members only rewrites the
-// table (a stream-ordered copy) -- the graph is rebuilt only when the largest member's
-// shared-memory need changes.
+// One batch step advances every member by one MPC step:
+//   - members large enough to fill the GPU alone (at least two waves of bricks) get
+//     their own launch of the single-box kernel;
+//   - the other members are packed, grouped by variant (kPackGroup boxes at most per
+//     group), and each group is one persistent launch of the packed kernel, which
+//     carries the boxes' arguments in kernel parameter space and lets its CTAs claim
+//     the group's bricks from a counter;
+//   - one small launch closes the step of every member (step counter, observables).
+// A batch step is captured in a CUDA graph of graph_steps steps; the graph is rebuilt
+// when the members (or their buffers) change.
 //
 // Member device memory can come from one arena allocated up front.  Memory a member
 // releases returns to the arena only after the stream it was released on has passed the
@@ -172,7 +175,9 @@ void arena_release(void* ctx, void* p, size_t bytes, void* stream) {
   static_cast<Arena*>(ctx)->release(p, bytes, static_cast<cudaStream_t>(stream));
 }
 
-constexpr int kTableBuffers = 3;  // pinned host copies of the work table in rotation
+constexpr int kTableBuffers = 3;  // pinned host copies of the member table in rotation
+constexpr int kSoloWaves = 2;     // members with this many waves of bricks run solo
+constexpr int kWaveCtasPerSm = 5; // CTAs per SM of a wave (the AT+a kernel's occupancy)
 
 }  // namespace
 
@@ -191,20 +196,29 @@ struct mpc_batch_s {
   Ctrl* ctrl_slab = nullptr;  // pinned control mirrors, one slot per member
   std::vector<int> free_slots;
   std::map<mpc_handle, int> slot_of;
-  BatchTable* table_dev = nullptr;
+  BatchTable* table_dev = nullptr;  // all members' arguments (closing kernel)
   BatchTable* table_host[kTableBuffers] = {};
   cudaEvent_t table_ev[kTableBuffers] = {};
   bool table_ev_live[kTableBuffers] = {};
   int table_next = 0;
   bool dirty = true;
-  int total_items = 0;
+  int total_items = 0;              // bricks of the packed members
   int64_t total_particles = 0;
   int num_sms = 0;
-  size_t smem = 0;
-  int ctas_per_sm = 0, grid = 0, adv_grid = 0;
+  int adv_grid = 0;
+  uint32_t* counters = nullptr;     // one work-claiming counter per packed group
+  struct Group {
+    int variant = 0;
+    size_t smem = 0;
+    int grid = 0, ctas_per_sm = 0;
+    PackTable table{};
+  };
+  std::vector<Group> groups;
+  std::vector<StepArgs> solo_args;  // arguments of the solo members' launches
+  int solo_bricks = 0;              // members with at least this many bricks run solo
+  bool pack_all = false;
   cudaGraphExec_t graph = nullptr;
-  size_t graph_smem = 0;
-  int graph_grid = 0;
+  bool graph_stale = true;
   int graph_builds = 0;
   std::map<std::string, std::pair<int, int>> tuned;
   std::string err;
@@ -229,53 +243,87 @@ size_t table_bytes(int nboxes) {
   return offsetof(BatchTable, args) + sizeof(StepArgs) * (size_t)nboxes;
 }
 
-// Rewrites the device work table when members or their buffers changed; reconfigures
-// the persistent kernel when the largest shared-memory need changed.
+// Rebuilds the launch plan when members or their buffers changed: solo members, packed
+// groups (sorted by variant and shared-memory need, kPackGroup boxes at most), and the
+// device table of all members for the closing kernel.
 mpc_status refresh(mpc_batch b) {
   // a member repaired or re-binned through its own handle has new buffers
   for (size_t i = 0; i < b->boxes.size() && !b->dirty; ++i)
     if (b->gens[i] != b->boxes[i]->buffers_gen) b->dirty = true;
   if (!b->dirty) return MPC_OK;
-  // a pinned buffer whose previous upload has executed
-  const int k = b->table_next;
+  const int k = b->table_next;  // a pinned buffer whose previous upload has executed
   b->table_next = (k + 1) % kTableBuffers;
   if (b->table_ev_live[k]) BCU(b, cudaEventSynchronize(b->table_ev[k]));
   BatchTable* t = b->table_host[k];
   const int n = (int)b->boxes.size();
+  std::vector<mpc_handle> packed;
+  b->solo_args.clear();
+  b->total_particles = 0;
   t->nboxes = n;
-  int64_t items = 0, parts = 0;
-  size_t smem = 0;
   for (int i = 0; i < n; ++i) {
     mpc_handle h = b->boxes[(size_t)i];
-    t->begin[i] = (int32_t)items;
-    items += h->g.nbricks;
-    parts += h->N;
-    t->args[i] = step_args(h);
     b->gens[(size_t)i] = h->buffers_gen;
-    smem = std::max(smem, step_smem_bytes(h->g));
+    t->args[i] = step_args(h);
+    b->total_particles += h->N;
+    if (!b->pack_all && h->g.nbricks >= b->solo_bricks) b->solo_args.push_back(t->args[i]);
+    else packed.push_back(h);
   }
-  if (items > INT32_MAX) return bfail(b, MPC_EINVAL, "the batch holds more than 2^31 bricks");
-  t->begin[n] = (int32_t)items;
-  t->total = (int32_t)items;
-  b->total_items = (int)items;
-  b->total_particles = parts;
+  std::stable_sort(packed.begin(), packed.end(), [](mpc_handle x, mpc_handle y) {
+    if (x->g.variant != y->g.variant) return x->g.variant < y->g.variant;
+    return step_smem_bytes(x->g) < step_smem_bytes(y->g);
+  });
+  b->groups.clear();
+  int64_t items = 0;
+  for (size_t i = 0; i < packed.size(); ++i) {
+    mpc_handle h = packed[i];
+    if (b->groups.empty() || b->groups.back().variant != h->g.variant ||
+        b->groups.back().table.n == kPackGroup) {
+      b->groups.emplace_back();
+      b->groups.back().variant = h->g.variant;
+    }
+    mpc_batch_s::Group& G = b->groups.back();
+    PackTable& P = G.table;
+    if (P.n == 0) P.begin[0] = 0;
+    P.args[P.n] = step_args(h);
+    P.begin[P.n + 1] = P.begin[P.n] + h->g.nbricks;
+    P.n += 1;
+    G.smem = std::max(G.smem, step_smem_bytes(h->g));
+    items += h->g.nbricks;
+  }
+  if ((int)b->groups.size() > b->max_boxes) return bfail(b, MPC_EINVAL, "too many packed groups");
+  BCU(b, configure_step_kernels(device_smem_limit(b->device)));
+  for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+    mpc_batch_s::Group& G = b->groups[gi];
+    G.table.counter = b->counters + gi;
+    BCU(b, packed_kernel_occupancy(G.variant, b->det, G.smem, &G.ctas_per_sm));
+    if (G.ctas_per_sm < 1) return bfail(b, MPC_EINVAL, "the packed step kernel does not fit on an SM");
+    G.grid = (int)std::min<int64_t>(G.table.begin[G.table.n], (int64_t)G.ctas_per_sm * b->num_sms);
+  }
+  b->total_items = (int)std::min<int64_t>(items, INT32_MAX);
   BCU(b, cudaMemcpyAsync(b->table_dev, t, table_bytes(n), cudaMemcpyHostToDevice, b->stream));
   BCU(b, cudaEventRecord(b->table_ev[k], b->stream));
   b->table_ev_live[k] = true;
-  if (n > 0 && smem != b->smem) {
-    int per_sm = 0;
-    BCU(b, configure_batch_kernel(b->det, smem, &per_sm));
-    if (per_sm < 1) return bfail(b, MPC_EINVAL, "the batched step kernel does not fit on an SM");
-    b->smem = smem;
-    b->ctas_per_sm = per_sm;
-    b->grid = per_sm * b->num_sms;
-  }
+  b->graph_stale = true;
   b->dirty = false;
   return MPC_OK;
 }
 
+// one batch step: the solo members' own kernels, one persistent launch per packed
+// group (their claim counters zeroed first), then the closing of every member's step
+cudaError_t launch_batch_step(mpc_batch b, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  for (const StepArgs& a : b->solo_args)
+    if (e == cudaSuccess) e = launch_step(a, s);
+  if (e == cudaSuccess && !b->groups.empty())
+    e = cudaMemsetAsync(b->counters, 0, sizeof(uint32_t) * b->groups.size(), s);
+  for (const mpc_batch_s::Group& G : b->groups)
+    if (e == cudaSuccess) e = launch_step_packed(G.table, G.variant, b->det, G.grid, G.smem, s);
+  if (e == cudaSuccess) e = launch_advance_batch(b->table_dev, b->adv_grid, s);
+  return e;
+}
+
 mpc_status build_graph(mpc_batch b) {
-  if (b->graph && b->graph_smem == b->smem && b->graph_grid == b->grid) return MPC_OK;
+  if (b->graph && !b->graph_stale) return MPC_OK;
   if (b->graph) {
     cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
@@ -283,8 +331,7 @@ mpc_status build_graph(mpc_batch b) {
   cudaGraph_t g = nullptr;
   BCU(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeRelaxed));
   for (int k = 0; k < b->graph_steps; ++k) {
-    cudaError_t e = launch_step_batch(b->table_dev, b->det, b->grid, b->smem, b->cap_stream);
-    if (e == cudaSuccess) e = launch_advance_batch(b->table_dev, b->adv_grid, b->cap_stream);
+    const cudaError_t e = launch_batch_step(b, b->cap_stream);
     if (e != cudaSuccess) {
       cudaStreamEndCapture(b->cap_stream, &g);
       if (g) cudaGraphDestroy(g);
@@ -295,8 +342,7 @@ mpc_status build_graph(mpc_batch b) {
   const cudaError_t e = cudaGraphInstantiate(&b->graph, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return bfail(b, MPC_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-  b->graph_smem = b->smem;
-  b->graph_grid = b->grid;
+  b->graph_stale = false;
   b->graph_builds += 1;
   return MPC_OK;
 }
@@ -312,8 +358,9 @@ std::string class_key(const mpc_params& p) {
 
 extern "C" {
 
-mpc_status mpc_autotune(const mpc_params* p, void* stream, int32_t* tile_particles,
-                        int32_t* threads_per_cell, double* ns_per_particle_step) {
+mpc_status mpc_autotune(const mpc_params* p, void* stream, uint64_t max_smem_bytes,
+                        int32_t* tile_particles, int32_t* threads_per_cell,
+                        double* ns_per_particle_step) {
   if (!p || !tile_particles || !threads_per_cell)
     return fail(nullptr, MPC_EINVAL, "params and outputs are required");
   int dev = 0;
@@ -338,6 +385,7 @@ mpc_status mpc_autotune(const mpc_params* p, void* stream, int32_t* tile_particl
     q.tile_particles = tile;
     q.threads_per_cell = 0;
     TRY(plan_box(&q, lim, g, N));
+    if (max_smem_bytes && step_smem_bytes(g) > max_smem_bytes) continue;
     const int t0 = g.tpc;
     for (int tpc : {t0 / 2, t0, t0 * 2, t0 * 4}) {
       if (tpc < 1 || tpc > 32) continue;
@@ -388,6 +436,7 @@ mpc_status mpc_batch_destroy(mpc_batch b) {
   if (b->graph) cudaGraphExecDestroy(b->graph);
   delete b->arena;
   if (b->table_dev) cudaFree(b->table_dev);
+  if (b->counters) cudaFree(b->counters);
   for (int k = 0; k < kTableBuffers; ++k) {
     if (b->table_host[k]) cudaFreeHost(b->table_host[k]);
     if (b->table_ev[k]) cudaEventDestroy(b->table_ev[k]);
@@ -405,7 +454,7 @@ mpc_status mpc_batch_create(const mpc_batch_config* cfg, void* stream, mpc_batch
   mpc_batch_config c{};
   if (cfg) c = *cfg;
   if (c.graph_steps < 0 || c.max_boxes < 0 || c.max_boxes > kMaxBatchBoxes || c.reserved != 0 ||
-      (c.flags & ~(uint32_t)(MPC_BATCH_DETERMINISTIC | MPC_BATCH_AUTOTUNE)))
+      (c.flags & ~(uint32_t)(MPC_BATCH_DETERMINISTIC | MPC_BATCH_AUTOTUNE | MPC_BATCH_PACK_ALL)))
     return bfail(nullptr, MPC_EINVAL, "invalid batch configuration");
   mpc_batch b = new (std::nothrow) mpc_batch_s();
   if (!b) return bfail(nullptr, MPC_ENOMEM, "host allocation failed");
@@ -421,11 +470,14 @@ mpc_status mpc_batch_create(const mpc_batch_config* cfg, void* stream, mpc_batch
   b->stream = static_cast<cudaStream_t>(stream);
   b->det = (c.flags & MPC_BATCH_DETERMINISTIC) != 0;
   b->autotune = (c.flags & MPC_BATCH_AUTOTUNE) != 0;
+  b->pack_all = (c.flags & MPC_BATCH_PACK_ALL) != 0;
   b->graph_steps = c.graph_steps > 0 ? c.graph_steps : 100;
   b->max_boxes = c.max_boxes > 0 ? c.max_boxes : kMaxBatchBoxes;
   if (cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess)
     return bail(MPC_ECUDA, "cannot query the SM count");
+
   b->adv_grid = b->num_sms;
+  b->solo_bricks = kSoloWaves * kWaveCtasPerSm * b->num_sms;
   if (cudaStreamCreateWithFlags(&b->adm_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     return bail(MPC_ECUDA, "stream creation failed");
@@ -436,7 +488,11 @@ mpc_status mpc_batch_create(const mpc_batch_config* cfg, void* stream, mpc_batch
   for (int k = b->max_boxes - 1; k >= 0; --k) b->free_slots.push_back(k);
   if (cudaMalloc(&b->table_dev, sizeof(BatchTable)) != cudaSuccess) {
     b->table_dev = nullptr;
-    return bail(MPC_ENOMEM, "device allocation failed: work table");
+    return bail(MPC_ENOMEM, "device allocation failed: member table");
+  }
+  if (cudaMalloc(&b->counters, sizeof(uint32_t) * (size_t)b->max_boxes) != cudaSuccess) {
+    b->counters = nullptr;
+    return bail(MPC_ENOMEM, "device allocation failed: claim counters");
   }
   for (int k = 0; k < kTableBuffers; ++k) {
     if (cudaMallocHost(&b->table_host[k], sizeof(BatchTable)) != cudaSuccess) {
@@ -475,7 +531,7 @@ mpc_status mpc_batch_add(mpc_batch b, const mpc_params* p, mpc_handle* out) {
     if (it == b->tuned.end()) {
       int32_t tile = 0, tpc = 0;
       double ns = 0.0;
-      if (mpc_autotune(&q, b->adm_stream, &tile, &tpc, &ns) != MPC_OK)
+      if (mpc_autotune(&q, b->adm_stream, 0, &tile, &tpc, &ns) != MPC_OK)
         return bfail(b, MPC_ECUDA, std::string("autotune: ") + mpc_last_error(nullptr));
       it = b->tuned.emplace(key, std::make_pair((int)tile, (int)tpc)).first;
     }
@@ -543,10 +599,7 @@ mpc_status mpc_batch_step(mpc_batch b, int64_t nsteps) {
     if (mpc_status st = build_graph(b); st != MPC_OK) return st;
     for (; n >= b->graph_steps; n -= b->graph_steps) BCU(b, cudaGraphLaunch(b->graph, b->stream));
   }
-  for (; n > 0; --n) {
-    BCU(b, launch_step_batch(b->table_dev, b->det, b->grid, b->smem, b->stream));
-    BCU(b, launch_advance_batch(b->table_dev, b->adv_grid, b->stream));
-  }
+  for (; n > 0; --n) BCU(b, launch_batch_step(b, b->stream));
   return MPC_OK;
 }
 
@@ -569,13 +622,10 @@ mpc_status mpc_batch_get_info(mpc_batch b, mpc_batch_info* out) {
   if (!b) return bfail(nullptr, MPC_EINVAL, "batch is NULL");
   if (!out) return bfail(b, MPC_EINVAL, "out is NULL");
   std::memset(out, 0, sizeof(*out));
-  int64_t items = 0, parts = 0;
-  for (mpc_handle h : b->boxes) {
-    items += h->g.nbricks;
-    parts += h->N;
-  }
+  int64_t parts = 0;
+  for (mpc_handle h : b->boxes) parts += h->N;
   out->n_boxes = (int32_t)b->boxes.size();
-  out->work_items = (int32_t)items;
+  out->work_items = b->total_items;
   out->n_particles = parts;
   if (b->arena) {
     b->arena->reclaim(false);
@@ -583,11 +633,15 @@ mpc_status mpc_batch_get_info(mpc_batch b, mpc_batch_info* out) {
     out->arena_used = b->arena->used();
     out->arena_largest_free = b->arena->largest_free();
   }
-  out->grid = b->grid;
-  out->ctas_per_sm = b->ctas_per_sm;
-  out->smem_bytes = (int32_t)b->smem;
+  for (const mpc_batch_s::Group& G : b->groups) {
+    out->grid += G.grid;
+    out->ctas_per_sm = std::max(out->ctas_per_sm, G.ctas_per_sm);
+    out->smem_bytes = std::max(out->smem_bytes, (int32_t)G.smem);
+  }
+  out->packed_launches = (int32_t)b->groups.size();
   out->graph_builds = b->graph_builds;
   out->tuned_classes = (int32_t)b->tuned.size();
+  out->solo_boxes = (int32_t)b->solo_args.size();
   return MPC_OK;
 }
 

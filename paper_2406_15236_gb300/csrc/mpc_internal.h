@@ -86,26 +86,37 @@ struct StepArgs {
   uint32_t* dbg_counts;   // ncells (debug)
 };
 
-// Work table of a batch: box k owns the work items (bricks) [begin[k], begin[k+1]).
+// Step arguments of every member of a batch (device memory), for the kernel that
+// closes each member's step.
 constexpr int kMaxBatchBoxes = 4096;
 struct BatchTable {
   int32_t nboxes;
-  int32_t total;
-  int32_t begin[kMaxBatchBoxes + 1];
   StepArgs args[kMaxBatchBoxes];
 };
 
+// Boxes of one packed launch, passed by value in kernel parameter space (at most 32 KB):
+// box k owns the work items [begin[k], begin[k+1]).
+constexpr int kPackGroup = 48;
+struct PackTable {
+  int32_t n;
+  uint32_t* counter;  // work-claiming counter, zero when the launch starts
+  int32_t begin[kPackGroup + 1];
+  StepArgs args[kPackGroup];
+};
+static_assert(sizeof(PackTable) <= 32000, "PackTable must fit in kernel parameter space");
+
 // launchers (mpc_step.cu)
 size_t step_smem_bytes(const Geom& g);
-cudaError_t configure_step_kernels(const Geom& g);
+// raises the dynamic shared-memory cap of every step kernel to the device limit
+cudaError_t configure_step_kernels(size_t max_dynamic_smem);
 cudaError_t launch_step(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_advance(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_store_i64(int64_t* p, int64_t v, cudaStream_t s);
-// batched step: sets the dynamic shared memory of the batched kernel and reports how
-// many of its CTAs fit on one SM
-cudaError_t configure_batch_kernel(bool det, size_t smem_bytes, int* ctas_per_sm);
-cudaError_t launch_step_batch(const BatchTable* t, bool det, int grid, size_t smem_bytes,
-                              cudaStream_t s);
+// packed step of many small boxes of one variant: CTAs of the kernel per SM, launch
+cudaError_t packed_kernel_occupancy(int variant, bool det, size_t smem_bytes, int* ctas_per_sm);
+cudaError_t launch_step_packed(const PackTable& t, int variant, bool det, int grid,
+                               size_t smem_bytes, cudaStream_t s);
+// closes the step of every member of a batch
 cudaError_t launch_advance_batch(const BatchTable* t, int grid, cudaStream_t s);
 
 // launchers (mpc_layout.cu)

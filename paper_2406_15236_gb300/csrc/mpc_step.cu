@@ -800,37 +800,29 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
   step_brick<VAR, DET, false>(a, blockIdx.x, smem, sh, phase);
 }
 
-// Many boxes of any variant in one persistent launch: the CTAs stride over the packed
-// list of (box, brick) work items; box k owns items [begin[k], begin[k+1]).
-template <bool DET>
-__global__ void __launch_bounds__(kThreads, 5) k_step_batch(const BatchTable* __restrict__ t) {
+// Many small boxes of one variant in one persistent launch.  The boxes' arguments
+// travel in kernel parameter space (PackTable, passed by value), so the per-box values
+// the hot loops read are uniform constant-bank loads like those of the single-box
+// kernel rather than per-thread registers.  CTAs claim work items (bricks of the
+// packed boxes, box k owning items [begin[k], begin[k+1])) from a counter that is zero
+// at launch; each CTA's claims increase, so its box index only moves forward.
+template <int VAR, bool DET>
+__global__ void __launch_bounds__(kThreads) k_step_packed(const __grid_constant__ PackTable p) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ BrickShared sh;
-  __shared__ int s_box;
+  __shared__ int s_w;
   if (threadIdx.x == 0) mbar_init(&sh.bar, 1);
   __syncthreads();
   uint32_t phase = 0;
-  const int total = t->total;
-  const int nboxes = t->nboxes;
-  for (int w = blockIdx.x; w < total; w += gridDim.x) {
-    if (threadIdx.x == 0) {
-      int lo = 0, hi = nboxes - 1;  // last box whose first item is <= w
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (t->begin[mid] <= w) lo = mid;
-        else hi = mid - 1;
-      }
-      s_box = lo;
-    }
+  const int total = p.begin[p.n];
+  int k = 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_w = (int)atomicAdd(p.counter, 1u);
     __syncthreads();
-    const int k = s_box;
-    const StepArgs& a = t->args[k];
-    const int b = w - t->begin[k];
-    bool ok;
-    if (a.g.variant == 0) ok = step_brick<0, DET, true>(a, b, smem, sh, phase);
-    else if (a.g.variant == 1) ok = step_brick<1, DET, true>(a, b, smem, sh, phase);
-    else ok = step_brick<2, DET, true>(a, b, smem, sh, phase);
-    if (!ok) return;
+    const int w = s_w;
+    if (w >= total) return;
+    while (k + 1 < p.n && p.begin[k + 1] <= w) ++k;
+    if (!step_brick<VAR, DET, true>(p.args[k], w - p.begin[k], smem, sh, phase)) return;
     // the next item's bulk copies overwrite shared memory this item wrote
     fence_proxy_async_smem();
     __syncthreads();
@@ -894,21 +886,26 @@ size_t step_smem_bytes(const Geom& g) {
   return layout_for<2>(g).total;
 }
 
-template <bool DET>
-cudaError_t set_step_smem(const Geom& g, size_t bytes) {
-  cudaError_t e;
-  if (g.variant == 0)
-    e = cudaFuncSetAttribute(k_step<0, DET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  else if (g.variant == 1)
-    e = cudaFuncSetAttribute(k_step<1, DET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  else
-    e = cudaFuncSetAttribute(k_step<2, DET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+// The dynamic shared-memory cap is a per-function attribute shared by every box in the
+// process: it is set once to the device's limit (the launch's own size still decides
+// occupancy), so boxes with different needs never lower each other's cap.
+cudaError_t configure_step_kernels(size_t max_dynamic_smem) {
+  const int v = (int)max_dynamic_smem;
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<0, false>, a, v);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<1, false>, a, v);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<2, false>, a, v);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<0, true>, a, v);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<1, true>, a, v);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<2, true>, a, v);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step_packed<0, false>, a, v);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step_packed<1, false>, a, v);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step_packed<2, false>, a, v);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step_packed<0, true>, a, v);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step_packed<1, true>, a, v);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step_packed<2, true>, a, v);
   return e;
-}
-
-cudaError_t configure_step_kernels(const Geom& g) {
-  const size_t bytes = step_smem_bytes(g);
-  return g.det ? set_step_smem<true>(g, bytes) : set_step_smem<false>(g, bytes);
 }
 
 template <bool DET>
@@ -938,24 +935,31 @@ cudaError_t launch_store_i64(int64_t* p, int64_t v, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t configure_batch_kernel(bool det, size_t smem_bytes, int* ctas_per_sm) {
-  cudaError_t e;
-  if (det) {
-    e = cudaFuncSetAttribute(k_step_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_step_batch<true>, kThreads, smem_bytes);
-  } else {
-    e = cudaFuncSetAttribute(k_step_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_step_batch<false>, kThreads, smem_bytes);
-  }
-  return e;
+template <bool DET>
+cudaError_t packed_occupancy_t(int variant, size_t smem_bytes, int* ctas_per_sm) {
+  if (variant == 0)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_step_packed<0, DET>, kThreads, smem_bytes);
+  if (variant == 1)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_step_packed<1, DET>, kThreads, smem_bytes);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_step_packed<2, DET>, kThreads, smem_bytes);
 }
 
-cudaError_t launch_step_batch(const BatchTable* t, bool det, int grid, size_t smem_bytes,
-                              cudaStream_t s) {
-  if (det) k_step_batch<true><<<grid, kThreads, smem_bytes, s>>>(t);
-  else k_step_batch<false><<<grid, kThreads, smem_bytes, s>>>(t);
+cudaError_t packed_kernel_occupancy(int variant, bool det, size_t smem_bytes, int* ctas_per_sm) {
+  return det ? packed_occupancy_t<true>(variant, smem_bytes, ctas_per_sm)
+             : packed_occupancy_t<false>(variant, smem_bytes, ctas_per_sm);
+}
+
+template <bool DET>
+void launch_packed_t(const PackTable& t, int variant, int grid, size_t smem_bytes, cudaStream_t s) {
+  if (variant == 0) k_step_packed<0, DET><<<grid, kThreads, smem_bytes, s>>>(t);
+  else if (variant == 1) k_step_packed<1, DET><<<grid, kThreads, smem_bytes, s>>>(t);
+  else k_step_packed<2, DET><<<grid, kThreads, smem_bytes, s>>>(t);
+}
+
+cudaError_t launch_step_packed(const PackTable& t, int variant, bool det, int grid,
+                               size_t smem_bytes, cudaStream_t s) {
+  if (det) launch_packed_t<true>(t, variant, grid, smem_bytes, s);
+  else launch_packed_t<false>(t, variant, grid, smem_bytes, s);
   return cudaGetLastError();
 }
 

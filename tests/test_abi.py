@@ -50,6 +50,9 @@ LAYOUT = [
     ("offsetof(mpc_batch_config, flags)", lambda: mpc.mpc_batch_config.flags.offset),
     ("offsetof(mpc_batch_info, grid)", lambda: mpc.mpc_batch_info.grid.offset),
     ("offsetof(mpc_batch_info, tuned_classes)", lambda: mpc.mpc_batch_info.tuned_classes.offset),
+    ("offsetof(mpc_batch_info, solo_boxes)", lambda: mpc.mpc_batch_info.solo_boxes.offset),
+    ("offsetof(mpc_batch_info, packed_launches)",
+     lambda: mpc.mpc_batch_info.packed_launches.offset),
 ]
 
 

@@ -215,3 +215,45 @@ def test_autotune_picks_a_candidate():
         assert b.info().tuned_classes == 2
         b.step(3)
         b.synchronize()
+
+
+def test_boxes_with_different_shared_memory_needs_coexist():
+    """Creating a box with a small shared-memory need must not break a box created
+    earlier with a larger one (the kernels' shared-memory cap is process-wide)."""
+    mpc = _mpc()
+    big = mpc.Simulation(L=16, n_c=20.0, variant=1, tile_particles=1280, seed=1)
+    small = mpc.Simulation(L=8, n_c=5.0, variant=0, tile_particles=320, seed=2)
+    big.step(3)
+    small.step(3)
+    big.synchronize()
+    small.synchronize()
+    assert big.get_state()[3] == 3 and small.get_state()[3] == 3
+    big.close()
+    small.close()
+
+
+def test_solo_members_match_packed_and_oracle():
+    """Members with at least two GPU waves of bricks get their own single-box launch
+    inside the batch step; their results are bit-identical to packing them (deterministic
+    mode) and match the oracle."""
+    mpc = _mpc()
+    big = dict(L=48, n_c=20.0, h=0.05, variant=1, seed=2001)
+    kws = [big, MIX[0], MIX[3]]
+    runs = []
+    for pack_all in (False, True):
+        with mpc.Batch(deterministic=True, graph_steps=8, pack_all=pack_all) as b:
+            boxes = [b.add(**kw) for kw in kws]
+            b.step(20)
+            runs.append(([_state(bx) for bx in boxes], b.info().solo_boxes))
+    assert runs[0][1] == 1 and runs[1][1] == 0
+    for a, c in zip(runs[0][0], runs[1][0]):
+        assert _same(a, c)
+    with mpc.Batch(graph_steps=8) as b:
+        boxes = [b.add(**kw) for kw in kws]
+        b.step(3)
+        pre = [bx.get_state()[:3] for bx in boxes]
+        b.step(1)
+        for kw, bx, p0 in zip(kws, boxes, pre):
+            X1, V1, id1, step = bx.get_state()
+            assert step == 4
+            par.check_step(par.oracle_params(**kw), p0, (X1, V1, id1), 3)
