@@ -305,6 +305,81 @@ mpc_status mpc_batch_get_info(mpc_batch b, mpc_batch_info* out);
 /* Text of the last error of a batch call (NULL: of the last failed mpc_batch_create). */
 const char* mpc_batch_last_error(mpc_batch b);
 
+/* ---- Serving: a continuous-batching request loop ----------------------------------
+ * The paper runs one system per job; a server takes simulation jobs (a box, a step
+ * count) with arrival times, admits each as soon as it has arrived and its device
+ * footprint fits the HBM budget (later small jobs may pass a head job that does not
+ * fit), keeps admitted jobs resident as members of one batch, advances all of them
+ * together in chunks of steps, stops each at its own step count, and retires it:
+ * its observables give a Green-Kubo shear viscosity, its memory returns to the budget,
+ * and waiting jobs are admitted between chunks while the next chunk runs on the GPU.
+ * MPC_SERVER_SEQUENTIAL runs the same jobs one at a time through mpc_create/mpc_step
+ * instead (the plain path, for comparison).  A server is used by one host thread. */
+typedef struct mpc_server_s* mpc_server;
+
+enum {
+  MPC_SERVER_DETERMINISTIC = 1u,  /* every job gets MPC_FLAG_DETERMINISTIC: a job's
+                                     results do not depend on the other jobs */
+  MPC_SERVER_SEQUENTIAL = 2u      /* one job at a time on the plain single-box path */
+};
+
+enum { MPC_JOB_QUEUED = 0, MPC_JOB_RUNNING = 1, MPC_JOB_DONE = 2, MPC_JOB_FAILED = 3 };
+enum { MPC_JOB_KEEP_SERIES = 1u, MPC_JOB_KEEP_STATE = 2u };
+
+typedef struct {
+  uint64_t hbm_budget_bytes;  /* device memory for resident jobs (one arena), > 0 */
+  int32_t chunk_steps;        /* most steps per scheduling round (graph size); 0 = 100 */
+  int32_t max_active;         /* most resident jobs; 0 = 4096 */
+  uint32_t flags;             /* MPC_SERVER_* */
+  int32_t reserved;           /* must be 0 */
+} mpc_server_config;
+
+typedef struct {
+  mpc_params params;          /* the box; MPC_FLAG_OBSERVABLES is added and the
+                                 observables ring holds every step */
+  int64_t steps;              /* steps to run, >= 1 */
+  double arrival_s;           /* seconds after the first mpc_server_run call */
+  uint32_t keep;              /* MPC_JOB_KEEP_*: keep the per-step observables and / or
+                                 the final state on the host for the caller */
+  int32_t reserved;           /* must be 0 */
+} mpc_job;
+
+typedef struct {
+  int32_t status;             /* MPC_JOB_* */
+  int32_t error;              /* mpc_status of a failed job */
+  double arrival_s, admit_s, finish_s;  /* finish: results on the host */
+  int64_t steps;
+  int64_t n_particles;
+  double eta_gk;              /* Green-Kubo shear viscosity, (V h / kT) [C(0)/2 +
+                                 sum_k C(k)] over the six off-diagonal stresses */
+  double temperature;         /* mean kinetic temperature over the run */
+} mpc_job_result;
+
+mpc_status mpc_server_create(const mpc_server_config* cfg, void* stream, mpc_server* out);
+mpc_status mpc_server_destroy(mpc_server s);
+
+/* Queue a job; *job_id receives its index (0, 1, ...).  No device work. */
+mpc_status mpc_server_submit(mpc_server s, const mpc_job* job, int64_t* job_id);
+
+/* Run the loop until every submitted job has finished or failed, or until timeout_s
+ * seconds of this call have passed (MPC_ETIMEOUT; running jobs stay resident and a
+ * later call continues).  Jobs that cannot fit the budget even alone fail with
+ * MPC_ENOMEM. */
+mpc_status mpc_server_run(mpc_server s, double timeout_s);
+
+mpc_status mpc_server_job(mpc_server s, int64_t job_id, mpc_job_result* out);
+
+/* The observables rows (16 doubles per step, as mpc_observable_series) of a finished
+ * job submitted with MPC_JOB_KEEP_SERIES; count >= its steps. */
+mpc_status mpc_server_job_series(mpc_server s, int64_t job_id, double* rows, int64_t count);
+
+/* The final state (host buffers: X 3N, V 3N, id N, sorted by unshifted cell) of a
+ * finished job submitted with MPC_JOB_KEEP_STATE. */
+mpc_status mpc_server_job_state(mpc_server s, int64_t job_id, uint32_t* X, float* V,
+                                uint32_t* id);
+
+const char* mpc_server_last_error(mpc_server s);
+
 /* Text of the last error on h (or of the last failed create when h is NULL). */
 const char* mpc_last_error(mpc_handle h);
 

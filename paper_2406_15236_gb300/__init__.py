@@ -88,6 +88,30 @@ class mpc_batch_info(ctypes.Structure):
                 ("packed_launches", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+MPC_SERVER_DETERMINISTIC, MPC_SERVER_SEQUENTIAL = 1, 2
+MPC_JOB_QUEUED, MPC_JOB_RUNNING, MPC_JOB_DONE, MPC_JOB_FAILED = 0, 1, 2, 3
+MPC_JOB_KEEP_SERIES, MPC_JOB_KEEP_STATE = 1, 2
+
+
+class mpc_server_config(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("chunk_steps", ctypes.c_int32),
+                ("max_active", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("reserved", ctypes.c_int32)]
+
+
+class mpc_job(ctypes.Structure):
+    _fields_ = [("params", mpc_params), ("steps", ctypes.c_int64), ("arrival_s", ctypes.c_double),
+                ("keep", ctypes.c_uint32), ("reserved", ctypes.c_int32)]
+
+
+class mpc_job_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("error", ctypes.c_int32),
+                ("arrival_s", ctypes.c_double), ("admit_s", ctypes.c_double),
+                ("finish_s", ctypes.c_double), ("steps", ctypes.c_int64),
+                ("n_particles", ctypes.c_int64), ("eta_gk", ctypes.c_double),
+                ("temperature", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -132,6 +156,15 @@ def lib():
     L.mpc_batch_get_info.argtypes = [vp, P(mpc_batch_info)]
     L.mpc_batch_last_error.argtypes = [vp]
     L.mpc_batch_last_error.restype = ctypes.c_char_p
+    L.mpc_server_create.argtypes = [P(mpc_server_config), vp, P(vp)]
+    L.mpc_server_destroy.argtypes = [vp]
+    L.mpc_server_submit.argtypes = [vp, P(mpc_job), P(ctypes.c_int64)]
+    L.mpc_server_run.argtypes = [vp, ctypes.c_double]
+    L.mpc_server_job.argtypes = [vp, ctypes.c_int64, P(mpc_job_result)]
+    L.mpc_server_job_series.argtypes = [vp, ctypes.c_int64, vp, ctypes.c_int64]
+    L.mpc_server_job_state.argtypes = [vp, ctypes.c_int64, vp, vp, vp]
+    L.mpc_server_last_error.argtypes = [vp]
+    L.mpc_server_last_error.restype = ctypes.c_char_p
     L.mpc_last_error.argtypes = [vp]
     L.mpc_last_error.restype = ctypes.c_char_p
     L.mpc_version.restype = ctypes.c_char_p
@@ -141,7 +174,9 @@ def lib():
                  "mpc_profile_step_kernel", "mpc_sort_by_cell_noalloc", "mpc_set_step_limit",
                  "mpc_footprint", "mpc_autotune", "mpc_batch_create", "mpc_batch_destroy",
                  "mpc_batch_add", "mpc_batch_remove", "mpc_batch_step", "mpc_batch_synchronize",
-                 "mpc_batch_get_info"):
+                 "mpc_batch_get_info", "mpc_server_create", "mpc_server_destroy",
+                 "mpc_server_submit", "mpc_server_run", "mpc_server_job",
+                 "mpc_server_job_series", "mpc_server_job_state"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -150,6 +185,12 @@ def lib():
 def _check(status, handle=None):
     if status != MPC_OK:
         msg = lib().mpc_last_error(handle)
+        raise MpcError(status, msg.decode() if msg else "")
+
+
+def _check_server(status, server=None):
+    if status != MPC_OK:
+        msg = lib().mpc_server_last_error(server)
         raise MpcError(status, msg.decode() if msg else "")
 
 
@@ -358,6 +399,48 @@ def mpc_batch_last_error(batch=None) -> str:
     return s.decode() if s else ""
 
 
+def mpc_server_create(config: mpc_server_config, stream=None):
+    srv = ctypes.c_void_p()
+    _check_server(lib().mpc_server_create(ctypes.byref(config), ctypes.c_void_p(stream or 0),
+                                          ctypes.byref(srv)))
+    return srv
+
+
+def mpc_server_destroy(server) -> None:
+    _check_server(lib().mpc_server_destroy(server), server)
+
+
+def mpc_server_submit(server, job: mpc_job) -> int:
+    jid = ctypes.c_int64()
+    _check_server(lib().mpc_server_submit(server, ctypes.byref(job), ctypes.byref(jid)), server)
+    return jid.value
+
+
+def mpc_server_run(server, timeout_s: float = 0.0) -> None:
+    _check_server(lib().mpc_server_run(server, float(timeout_s)), server)
+
+
+def mpc_server_job(server, job_id: int) -> mpc_job_result:
+    r = mpc_job_result()
+    _check_server(lib().mpc_server_job(server, int(job_id), ctypes.byref(r)), server)
+    return r
+
+
+def mpc_server_job_series(server, job_id: int, rows: np.ndarray) -> None:
+    _check_server(lib().mpc_server_job_series(server, int(job_id), rows.ctypes.data, rows.shape[0]),
+                  server)
+
+
+def mpc_server_job_state(server, job_id: int, X, V, ids) -> None:
+    _check_server(lib().mpc_server_job_state(server, int(job_id), _addr(X), _addr(V), _addr(ids)),
+                  server)
+
+
+def mpc_server_last_error(server=None) -> str:
+    s = lib().mpc_server_last_error(server)
+    return s.decode() if s else ""
+
+
 # --- convenience wrapper -----------------------------------------------------------------
 
 class Box:
@@ -492,6 +575,83 @@ class Batch:
             for b in self.boxes:
                 b.handle = None
             self.boxes = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Server:
+    """Continuous-batching request loop: jobs (box parameters, step count, arrival time)
+    are admitted by HBM budget, advanced together while resident, and retired with a
+    Green-Kubo viscosity."""
+
+    def __init__(self, hbm_budget_bytes, chunk_steps=0, max_active=0, deterministic=False,
+                 sequential=False, stream=None):
+        import torch
+
+        cfg = mpc_server_config()
+        cfg.hbm_budget_bytes = int(hbm_budget_bytes)
+        cfg.chunk_steps = int(chunk_steps)
+        cfg.max_active = int(max_active)
+        cfg.flags = (MPC_SERVER_DETERMINISTIC if deterministic else 0) | \
+            (MPC_SERVER_SEQUENTIAL if sequential else 0)
+        cfg.reserved = 0
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.handle = mpc_server_create(cfg, stream)
+        self.steps = []
+        self.N = []
+
+    def submit(self, steps, arrival_s=0.0, keep_series=False, keep_state=False, **kw) -> int:
+        job = mpc_job()
+        job.params = make_params(**kw)
+        job.steps = int(steps)
+        job.arrival_s = float(arrival_s)
+        job.keep = (MPC_JOB_KEEP_SERIES if keep_series else 0) | \
+            (MPC_JOB_KEEP_STATE if keep_state else 0)
+        job.reserved = 0
+        jid = mpc_server_submit(self.handle, job)
+        self.steps.append(int(steps))
+        L = job.params.L
+        self.N.append(int(round(L[0] * L[1] * L[2] * job.params.n_c)))
+        return jid
+
+    def run(self, timeout_s: float = 0.0) -> None:
+        mpc_server_run(self.handle, timeout_s)
+
+    def job(self, job_id: int) -> dict:
+        r = mpc_server_job(self.handle, job_id)
+        return {"status": r.status, "error": r.error, "arrival_s": r.arrival_s,
+                "admit_s": r.admit_s, "finish_s": r.finish_s, "steps": r.steps,
+                "n_particles": r.n_particles, "eta_gk": r.eta_gk, "temperature": r.temperature,
+                "latency_s": r.finish_s - r.arrival_s}
+
+    def series(self, job_id: int) -> np.ndarray:
+        rows = np.zeros((self.steps[job_id], 16), dtype=np.float64)
+        mpc_server_job_series(self.handle, job_id, rows)
+        return rows
+
+    def state(self, job_id: int):
+        N = self.N[job_id]
+        X = np.empty((3, N), dtype=np.uint32)
+        V = np.empty((3, N), dtype=np.float32)
+        ids = np.empty(N, dtype=np.uint32)
+        mpc_server_job_state(self.handle, job_id, X, V, ids)
+        return X, V, ids
+
+    def close(self):
+        if self.handle is not None:
+            mpc_server_destroy(self.handle)
+            self.handle = None
 
     def __del__(self):
         try:

@@ -53,6 +53,13 @@ LAYOUT = [
     ("offsetof(mpc_batch_info, solo_boxes)", lambda: mpc.mpc_batch_info.solo_boxes.offset),
     ("offsetof(mpc_batch_info, packed_launches)",
      lambda: mpc.mpc_batch_info.packed_launches.offset),
+    ("sizeof(mpc_server_config)", lambda: ctypes.sizeof(mpc.mpc_server_config)),
+    ("sizeof(mpc_job)", lambda: ctypes.sizeof(mpc.mpc_job)),
+    ("sizeof(mpc_job_result)", lambda: ctypes.sizeof(mpc.mpc_job_result)),
+    ("offsetof(mpc_job, steps)", lambda: mpc.mpc_job.steps.offset),
+    ("offsetof(mpc_job, keep)", lambda: mpc.mpc_job.keep.offset),
+    ("offsetof(mpc_job_result, eta_gk)", lambda: mpc.mpc_job_result.eta_gk.offset),
+    ("offsetof(mpc_server_config, flags)", lambda: mpc.mpc_server_config.flags.offset),
 ]
 
 
@@ -122,3 +129,15 @@ def test_invalid_batch_config_rejected_without_device():
         mpc.mpc_batch_create(cfg)
     assert e.value.status == mpc.MPC_EINVAL
     assert mpc.mpc_batch_last_error()
+
+
+def test_invalid_server_config_rejected_without_device():
+    cfg = mpc.mpc_server_config()
+    cfg.hbm_budget_bytes = 0
+    with pytest.raises(mpc.MpcError) as e:
+        mpc.mpc_server_create(cfg)
+    assert e.value.status == mpc.MPC_EINVAL
+    assert mpc.mpc_server_last_error()
+    lib = mpc.lib()
+    assert lib.mpc_server_run(None, 1.0) == mpc.MPC_EINVAL
+    assert lib.mpc_server_destroy(None) == mpc.MPC_OK

@@ -73,3 +73,24 @@ def test_srd_a_viscosity_matches_printed_value():
     eta, err = _mean_eta(2, 50.0, 0.02, L=48, steps=2600)
     print(f"SRD+a shear-wave eta = {eta:.2f} +- {err:.2f}; paper 111.3")
     assert abs(eta - 111.3) / 111.3 < 0.02
+
+
+def test_green_kubo_viscosity_of_served_boxes():
+    """The per-job Green-Kubo viscosity the server reports (stress autocorrelation of the
+    streaming + collision stress, the estimator used for batched and served viscosity
+    jobs) agrees with the SRD closed form: eight independent L = 12 boxes, 20,000 steps
+    each, N_c 10, h 0.1, alpha 130 deg."""
+    import torch
+
+    import paper_2406_15236_gb300 as mpc
+
+    torch.cuda.set_device(0)
+    with mpc.Server(8 << 30, chunk_steps=100) as srv:
+        ids = [srv.submit(steps=20000, L=12, n_c=10.0, h=0.1, alpha_deg=130.0, variant=0,
+                          seed=300 + k) for k in range(8)]
+        srv.run(timeout_s=600.0)
+        etas = np.array([srv.job(i)["eta_gk"] for i in ids])
+    mean, err = etas.mean(), etas.std(ddof=1) / np.sqrt(len(etas))
+    ref = eta_srd(10, 0.1, 130)
+    print(f"Green-Kubo eta {mean:.3f} +- {err:.3f} (closed form {ref:.3f}); boxes {etas}")
+    assert abs(mean - ref) < max(3 * err, 0.02 * ref) + 0.03 * ref
