@@ -60,6 +60,7 @@ def parse_args(argv=None):
     ap.add_argument("--batch-boxes", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=100)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--serve-jobs", type=int, default=24)
     return ap.parse_args(argv)
 
 
@@ -297,7 +298,8 @@ def run_batched(args, mpc, torch) -> dict:
     members = [batch.add(**kw) for kw in boxes]
     t_setup = time.perf_counter() - t0
     total_n = sum(m.N for m in members)
-    batch.step(K)  # warm-up: one graph of K steps
+    batch.step(K)  # warm-up: K steps on the launch plan, then K more through its graph
+    batch.step(K)
     batch.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -307,12 +309,12 @@ def run_batched(args, mpc, torch) -> dict:
     batch.synchronize()
     ms_batch = e0.elapsed_time(e1)
     info = batch.info()
-    steps_ok = all(m.get_state()[3] == 2 * K for m in members[:4])
+    steps_ok = all(m.get_state()[3] == 3 * K for m in members[:4])
     batch.close()
 
     sims = [mpc.Simulation(graph_steps=K, **kw) for kw in boxes]
     for s_ in sims:
-        s_.step(3)
+        s_.step(K)  # warm-up, including the capture of each box's K-step graph
     for s_ in sims:
         s_.synchronize()
     torch.cuda.synchronize()
@@ -343,6 +345,86 @@ def run_batched(args, mpc, torch) -> dict:
         "setup_s_incl_autotune": t_setup,
         "gpu_launches_per_step": info.solo_boxes + info.packed_launches + 1,
         "steps_check": steps_ok}
+
+
+# --- serving ---------------------------------------------------------------------------------------
+
+def serving_trace(n: int, rate: float, seed: int):
+    """Viscosity-measurement jobs with Poisson arrivals (mean `rate` per s, the first at
+    t = 0): periodic box, L uniform in {16, ..., 96}, N_c = 10, variant / alpha / h as in
+    the batched ensemble, steps log-uniform in [1000, 20000], seeds 5000 + i."""
+    import numpy as np
+
+    rng = np.random.default_rng(seed)
+    t = np.concatenate([[0.0], np.cumsum(rng.exponential(1.0 / rate, n - 1))])
+    Ls = rng.integers(16, 97, n)
+    kinds = rng.integers(0, len(BATCH_KINDS), n)
+    hs = rng.choice([0.02, 0.05, 0.1], n)
+    steps = np.exp(rng.uniform(np.log(1000.0), np.log(20000.0), n)).astype(int)
+    jobs = []
+    for i in range(n):
+        name, alpha = BATCH_KINDS[int(kinds[i])]
+        jobs.append(dict(L=int(Ls[i]), n_c=10.0, h=float(hs[i]), alpha_deg=alpha,
+                         variant=1 if name == "AT+a" else 0, seed=5000 + i, box_id=i,
+                         steps=int(steps[i]), arrival_s=float(t[i])))
+    return jobs
+
+
+def serve_once(mpc, jobs, budget, sequential: bool, **policy) -> dict:
+    import numpy as np
+
+    with mpc.Server(budget, chunk_steps=100, sequential=sequential, **policy) as srv:
+        ids = [srv.submit(**j) for j in jobs]
+        srv.run(timeout_s=900.0)
+        res = [srv.job(i) for i in ids]
+        stats = srv.stats()
+    done = [r for r in res if r["status"] == mpc.MPC_JOB_DONE]
+    lat = np.array([r["latency_s"] for r in done])
+    makespan = max(r["finish_s"] for r in done)
+    work = sum(r["n_particles"] * r["steps"] for r in done)
+    return {"jobs_done": len(done), "jobs_failed": len(res) - len(done),
+            "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)),
+            "mean_latency_s": float(lat.mean()), "makespan_s": makespan,
+            "jobs_per_s": len(done) / makespan, "particle_steps_per_s": work / makespan,
+            "loop": None if sequential else stats}
+
+
+def run_serving(args, mpc) -> dict:
+    """The served form (continuous batching under a 150 GB HBM budget; by default the jobs
+    with the least remaining work step first, 16M particles at a time) against the same
+    job trace run one job at a time on the plain path, at the stated arrival rate (more
+    work than the GPU can do: latency grows with the queue) and at 70 % of the served
+    throughput measured on the first trace.  At the stated rate the served form is also
+    run with every resident job stepping in every chunk."""
+    budget = 150 * 10**9
+    out = {"workload": "viscosity jobs: L uniform in {16..96}, N_c=10, SRD 90/130 deg or AT+a, "
+                       "h in {0.02,0.05,0.1}, steps log-uniform 1k-20k, Poisson arrivals; "
+                       f"{args.serve_jobs} jobs per trace (seeded), HBM budget 150 GB",
+           "budget_bytes": budget, "chunk_steps": 100}
+    stated = serving_trace(args.serve_jobs, 20.0, seed=5)
+    served = serve_once(mpc, stated, budget, False)
+    plain = serve_once(mpc, stated, budget, True)
+    share = serve_once(mpc, stated, budget, False, share_all=True)
+    out["stated_rate_20_per_s"] = {"served": served, "sequential_plain": plain,
+                                   "served_share_all": share,
+                                   "p99_ratio_plain_over_served":
+                                       plain["p99_latency_s"] / served["p99_latency_s"],
+                                   "jobs_per_s_ratio": served["jobs_per_s"] / plain["jobs_per_s"],
+                                   "p50_ratio_plain_over_served":
+                                       plain["p50_latency_s"] / served["p50_latency_s"]}
+    rate = 0.7 * served["jobs_per_s"]
+    light = serving_trace(args.serve_jobs, rate, seed=6)
+    served = serve_once(mpc, light, budget, False)
+    plain = serve_once(mpc, light, budget, True)
+    out[f"rate_70pct_of_capacity"] = {"arrival_rate_per_s": rate, "served": served,
+                                      "sequential_plain": plain,
+                                      "p99_ratio_plain_over_served":
+                                          plain["p99_latency_s"] / served["p99_latency_s"],
+                                      "p50_ratio_plain_over_served":
+                                          plain["p50_latency_s"] / served["p50_latency_s"],
+                                      "jobs_per_s_ratio": served["jobs_per_s"] / plain["jobs_per_s"]}
+    return out
 
 
 # --- our arm ----------------------------------------------------------------------------------------
@@ -449,6 +531,9 @@ def run_ours(args):
     batched = None
     if rank == 0 and world == 1 and not args.no_batch:
         batched = run_batched(args, mpc, torch)
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serve:
+        serving = run_serving(args, mpc)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -464,7 +549,7 @@ def run_ours(args):
                 "clocks": clk,
                 "checks": {"momentum": [float(x) for x in obs["momentum"]],
                            "temperature": obs["temperature"], "step": obs["step"]},
-                "batched": batched}
+                "batched": batched, "serving": serving}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -273,7 +273,7 @@ typedef struct {
   int32_t tuned_classes;
   int32_t solo_boxes;       /* members stepped by their own single-box launch */
   int32_t packed_launches;  /* persistent launches per step for the packed members */
-  int32_t reserved;
+  float plan_ms;            /* host time spent re-planning steps and capturing graphs */
 } mpc_batch_info;
 
 /* Create an empty batch on `stream` (cudaStream_t or NULL). */
@@ -309,8 +309,8 @@ const char* mpc_batch_last_error(mpc_batch b);
  * The paper runs one system per job; a server takes simulation jobs (a box, a step
  * count) with arrival times, admits each as soon as it has arrived and its device
  * footprint fits the HBM budget (later small jobs may pass a head job that does not
- * fit), keeps admitted jobs resident as members of one batch, advances all of them
- * together in chunks of steps, stops each at its own step count, and retires it:
+ * fit), keeps admitted jobs resident as members of one batch, advances them together
+ * in chunks of steps, stops each at its own step count, and retires it:
  * its observables give a Green-Kubo shear viscosity, its memory returns to the budget,
  * and waiting jobs are admitted between chunks while the next chunk runs on the GPU.
  * MPC_SERVER_SEQUENTIAL runs the same jobs one at a time through mpc_create/mpc_step
@@ -320,8 +320,16 @@ typedef struct mpc_server_s* mpc_server;
 enum {
   MPC_SERVER_DETERMINISTIC = 1u,  /* every job gets MPC_FLAG_DETERMINISTIC: a job's
                                      results do not depend on the other jobs */
-  MPC_SERVER_SEQUENTIAL = 2u      /* one job at a time on the plain single-box path */
+  MPC_SERVER_SEQUENTIAL = 2u,     /* one job at a time on the plain single-box path */
+  MPC_SERVER_SHARE_ALL = 4u,      /* every resident job steps in every chunk */
+  MPC_SERVER_FIRST_COME = 8u      /* pick stepping jobs in arrival order instead of by
+                                     least remaining work */
 };
+/* By default a chunk steps the resident jobs with the least remaining work (steps x
+ * particles) until they hold fill_kparticles thousand particles (default 16M: enough
+ * jobs that their launches overlap and keep every SM busy) and holds the others at their
+ * current step.  Short jobs then finish early (low median latency) while the GPU stays
+ * full (throughput, and with it the longest latency under load). */
 
 enum { MPC_JOB_QUEUED = 0, MPC_JOB_RUNNING = 1, MPC_JOB_DONE = 2, MPC_JOB_FAILED = 3 };
 enum { MPC_JOB_KEEP_SERIES = 1u, MPC_JOB_KEEP_STATE = 2u };
@@ -331,7 +339,8 @@ typedef struct {
   int32_t chunk_steps;        /* most steps per scheduling round (graph size); 0 = 100 */
   int32_t max_active;         /* most resident jobs; 0 = 4096 */
   uint32_t flags;             /* MPC_SERVER_* */
-  int32_t reserved;           /* must be 0 */
+  int32_t fill_kparticles;    /* particles (in thousands) the stepping jobs of a chunk
+                                 should hold; 0 = 16000 */
 } mpc_server_config;
 
 typedef struct {
@@ -355,6 +364,16 @@ typedef struct {
   double temperature;         /* mean kinetic temperature over the run */
 } mpc_job_result;
 
+typedef struct {
+  int64_t chunks;        /* chunks enqueued by the batched loop */
+  int64_t chunk_steps;   /* batch steps in them */
+  double gpu_ms;         /* device time of the chunks (CUDA events) */
+  double host_gap_ms;    /* wall time the device waited for the host between chunks */
+  double plan_ms;        /* host time re-planning launches and capturing graphs */
+  int32_t graph_builds;
+  int32_t reserved;
+} mpc_server_stats;
+
 mpc_status mpc_server_create(const mpc_server_config* cfg, void* stream, mpc_server* out);
 mpc_status mpc_server_destroy(mpc_server s);
 
@@ -368,6 +387,7 @@ mpc_status mpc_server_submit(mpc_server s, const mpc_job* job, int64_t* job_id);
 mpc_status mpc_server_run(mpc_server s, double timeout_s);
 
 mpc_status mpc_server_job(mpc_server s, int64_t job_id, mpc_job_result* out);
+mpc_status mpc_server_get_stats(mpc_server s, mpc_server_stats* out);
 
 /* The observables rows (16 doubles per step, as mpc_observable_series) of a finished
  * job submitted with MPC_JOB_KEEP_SERIES; count >= its steps. */

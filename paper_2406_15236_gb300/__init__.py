@@ -85,10 +85,11 @@ class mpc_batch_info(ctypes.Structure):
                 ("grid", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("smem_bytes", ctypes.c_int32), ("graph_builds", ctypes.c_int32),
                 ("tuned_classes", ctypes.c_int32), ("solo_boxes", ctypes.c_int32),
-                ("packed_launches", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("packed_launches", ctypes.c_int32), ("plan_ms", ctypes.c_float)]
 
 
-MPC_SERVER_DETERMINISTIC, MPC_SERVER_SEQUENTIAL = 1, 2
+MPC_SERVER_DETERMINISTIC, MPC_SERVER_SEQUENTIAL, MPC_SERVER_SHARE_ALL = 1, 2, 4
+MPC_SERVER_FIRST_COME = 8
 MPC_JOB_QUEUED, MPC_JOB_RUNNING, MPC_JOB_DONE, MPC_JOB_FAILED = 0, 1, 2, 3
 MPC_JOB_KEEP_SERIES, MPC_JOB_KEEP_STATE = 1, 2
 
@@ -96,7 +97,7 @@ MPC_JOB_KEEP_SERIES, MPC_JOB_KEEP_STATE = 1, 2
 class mpc_server_config(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("chunk_steps", ctypes.c_int32),
                 ("max_active", ctypes.c_int32), ("flags", ctypes.c_uint32),
-                ("reserved", ctypes.c_int32)]
+                ("fill_kparticles", ctypes.c_int32)]
 
 
 class mpc_job(ctypes.Structure):
@@ -110,6 +111,13 @@ class mpc_job_result(ctypes.Structure):
                 ("finish_s", ctypes.c_double), ("steps", ctypes.c_int64),
                 ("n_particles", ctypes.c_int64), ("eta_gk", ctypes.c_double),
                 ("temperature", ctypes.c_double)]
+
+
+class mpc_server_stats(ctypes.Structure):
+    _fields_ = [("chunks", ctypes.c_int64), ("chunk_steps", ctypes.c_int64),
+                ("gpu_ms", ctypes.c_double), ("host_gap_ms", ctypes.c_double),
+                ("plan_ms", ctypes.c_double), ("graph_builds", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -161,6 +169,7 @@ def lib():
     L.mpc_server_submit.argtypes = [vp, P(mpc_job), P(ctypes.c_int64)]
     L.mpc_server_run.argtypes = [vp, ctypes.c_double]
     L.mpc_server_job.argtypes = [vp, ctypes.c_int64, P(mpc_job_result)]
+    L.mpc_server_get_stats.argtypes = [vp, P(mpc_server_stats)]
     L.mpc_server_job_series.argtypes = [vp, ctypes.c_int64, vp, ctypes.c_int64]
     L.mpc_server_job_state.argtypes = [vp, ctypes.c_int64, vp, vp, vp]
     L.mpc_server_last_error.argtypes = [vp]
@@ -176,7 +185,7 @@ def lib():
                  "mpc_batch_add", "mpc_batch_remove", "mpc_batch_step", "mpc_batch_synchronize",
                  "mpc_batch_get_info", "mpc_server_create", "mpc_server_destroy",
                  "mpc_server_submit", "mpc_server_run", "mpc_server_job",
-                 "mpc_server_job_series", "mpc_server_job_state"):
+                 "mpc_server_job_series", "mpc_server_job_state", "mpc_server_get_stats"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -426,6 +435,12 @@ def mpc_server_job(server, job_id: int) -> mpc_job_result:
     return r
 
 
+def mpc_server_get_stats(server) -> mpc_server_stats:
+    st = mpc_server_stats()
+    _check_server(lib().mpc_server_get_stats(server, ctypes.byref(st)), server)
+    return st
+
+
 def mpc_server_job_series(server, job_id: int, rows: np.ndarray) -> None:
     _check_server(lib().mpc_server_job_series(server, int(job_id), rows.ctypes.data, rows.shape[0]),
                   server)
@@ -595,7 +610,8 @@ class Server:
     Green-Kubo viscosity."""
 
     def __init__(self, hbm_budget_bytes, chunk_steps=0, max_active=0, deterministic=False,
-                 sequential=False, stream=None):
+                 sequential=False, share_all=False, first_come=False, fill_kparticles=0,
+                 stream=None):
         import torch
 
         cfg = mpc_server_config()
@@ -603,8 +619,10 @@ class Server:
         cfg.chunk_steps = int(chunk_steps)
         cfg.max_active = int(max_active)
         cfg.flags = (MPC_SERVER_DETERMINISTIC if deterministic else 0) | \
-            (MPC_SERVER_SEQUENTIAL if sequential else 0)
-        cfg.reserved = 0
+            (MPC_SERVER_SEQUENTIAL if sequential else 0) | \
+            (MPC_SERVER_SHARE_ALL if share_all else 0) | \
+            (MPC_SERVER_FIRST_COME if first_come else 0)
+        cfg.fill_kparticles = int(fill_kparticles)
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
         self.handle = mpc_server_create(cfg, stream)
@@ -634,6 +652,10 @@ class Server:
                 "admit_s": r.admit_s, "finish_s": r.finish_s, "steps": r.steps,
                 "n_particles": r.n_particles, "eta_gk": r.eta_gk, "temperature": r.temperature,
                 "latency_s": r.finish_s - r.arrival_s}
+
+    def stats(self) -> dict:
+        st = mpc_server_get_stats(self.handle)
+        return {k: getattr(st, k) for k, _ in mpc_server_stats._fields_ if k != "reserved"}
 
     def series(self, job_id: int) -> np.ndarray:
         rows = np.zeros((self.steps[job_id], 16), dtype=np.float64)

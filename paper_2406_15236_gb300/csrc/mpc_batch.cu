@@ -8,14 +8,17 @@
 //     carries the boxes' arguments in kernel parameter space and lets its CTAs claim
 //     the group's bricks from a counter;
 //   - one small launch closes the step of every member (step counter, observables).
-// A batch step is captured in a CUDA graph of graph_steps steps; the graph is rebuilt
-// when the members (or their buffers) change.
+// Members at their step limit are left out of the launches.  A batch step is captured
+// in a CUDA graph of graph_steps steps once the same launch plan is used a second time;
+// the plan (and the graph) change when members, their buffers or their stepping state
+// change.
 //
 // Member device memory can come from one arena allocated up front.  Memory a member
 // releases returns to the arena only after the stream it was released on has passed the
 // release point (an event per release), so a member can be removed while steps that
 // still read it are queued.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
@@ -176,6 +179,7 @@ void arena_release(void* ctx, void* p, size_t bytes, void* stream) {
 }
 
 constexpr int kTableBuffers = 3;  // pinned host copies of the member table in rotation
+constexpr int kBranches = 4;      // concurrent streams for the launches of one step
 constexpr int kSoloWaves = 2;     // members with this many waves of bricks run solo
 constexpr int kWaveCtasPerSm = 5; // CTAs per SM of a wave (the AT+a kernel's occupancy)
 
@@ -186,6 +190,10 @@ struct mpc_batch_s {
   cudaStream_t stream = nullptr;      // steps
   cudaStream_t adm_stream = nullptr;  // member creation (overlaps queued steps)
   cudaStream_t cap_stream = nullptr;  // graph capture
+  cudaStream_t branch[kBranches] = {};  // forked streams of one step's launches
+  cudaEvent_t fork_ev = nullptr, join_ev[kBranches] = {};
+  std::vector<int> unit_branch;  // branch of each solo launch, then of each packed group
+  int n_branches = 0;
   bool det = false, autotune = false;
   int graph_steps = 100;
   int max_boxes = kMaxBatchBoxes;
@@ -193,6 +201,7 @@ struct mpc_batch_s {
   mpc_allocator alloc{};
   std::vector<mpc_handle> boxes;
   std::vector<uint64_t> gens;  // buffers_gen of each member at the last table upload
+  std::vector<char> stepping;  // members below their step limit at the last plan
   Ctrl* ctrl_slab = nullptr;  // pinned control mirrors, one slot per member
   std::vector<int> free_slots;
   std::map<mpc_handle, int> slot_of;
@@ -219,7 +228,9 @@ struct mpc_batch_s {
   bool pack_all = false;
   cudaGraphExec_t graph = nullptr;
   bool graph_stale = true;
+  int plan_uses = 0;  // batch-step calls on the current plan; graphs from the second on
   int graph_builds = 0;
+  double plan_ms = 0.0;  // host time spent re-planning and capturing graphs
   std::map<std::string, std::pair<int, int>> tuned;
   std::string err;
 };
@@ -243,13 +254,37 @@ size_t table_bytes(int nboxes) {
   return offsetof(BatchTable, args) + sizeof(StepArgs) * (size_t)nboxes;
 }
 
+// The launches of one step (solo members and packed groups) are independent: they are
+// spread over up to kBranches forked streams (largest first, each to the least loaded
+// branch) so that one launch's last partial wave overlaps the next launch.
+void assign_branches(mpc_batch b) {
+  const size_t units = b->solo_args.size() + b->groups.size();
+  b->unit_branch.assign(units, 0);
+  b->n_branches = (int)std::min<size_t>(units, kBranches);
+  if (b->n_branches <= 1) return;
+  std::vector<std::pair<int64_t, size_t>> work;  // (bricks, unit)
+  for (size_t i = 0; i < b->solo_args.size(); ++i) work.push_back({b->solo_args[i].g.nbricks, i});
+  for (size_t i = 0; i < b->groups.size(); ++i)
+    work.push_back({b->groups[i].table.begin[b->groups[i].table.n], b->solo_args.size() + i});
+  std::stable_sort(work.begin(), work.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+  std::vector<int64_t> load((size_t)b->n_branches, 0);
+  for (const auto& w : work) {
+    const size_t k = (size_t)(std::min_element(load.begin(), load.end()) - load.begin());
+    b->unit_branch[w.second] = (int)k;
+    load[k] += w.first;
+  }
+}
+
 // Rebuilds the launch plan when members or their buffers changed: solo members, packed
 // groups (sorted by variant and shared-memory need, kPackGroup boxes at most), and the
 // device table of all members for the closing kernel.
 mpc_status refresh(mpc_batch b) {
-  // a member repaired or re-binned through its own handle has new buffers
-  for (size_t i = 0; i < b->boxes.size() && !b->dirty; ++i)
-    if (b->gens[i] != b->boxes[i]->buffers_gen) b->dirty = true;
+  // a member repaired or re-binned through its own handle has new buffers; a member at
+  // its step limit is left out of the launches until its limit moves
+  for (size_t i = 0; i < b->boxes.size() && !b->dirty; ++i) {
+    const mpc_handle h = b->boxes[i];
+    if (b->gens[i] != h->buffers_gen || b->stepping[i] != (h->limit > h->target_step)) b->dirty = true;
+  }
   if (!b->dirty) return MPC_OK;
   const int k = b->table_next;  // a pinned buffer whose previous upload has executed
   b->table_next = (k + 1) % kTableBuffers;
@@ -263,8 +298,10 @@ mpc_status refresh(mpc_batch b) {
   for (int i = 0; i < n; ++i) {
     mpc_handle h = b->boxes[(size_t)i];
     b->gens[(size_t)i] = h->buffers_gen;
+    b->stepping[(size_t)i] = h->limit > h->target_step;
     t->args[i] = step_args(h);
     b->total_particles += h->N;
+    if (!b->stepping[(size_t)i]) continue;
     if (!b->pack_all && h->g.nbricks >= b->solo_bricks) b->solo_args.push_back(t->args[i]);
     else packed.push_back(h);
   }
@@ -303,7 +340,9 @@ mpc_status refresh(mpc_batch b) {
   BCU(b, cudaMemcpyAsync(b->table_dev, t, table_bytes(n), cudaMemcpyHostToDevice, b->stream));
   BCU(b, cudaEventRecord(b->table_ev[k], b->stream));
   b->table_ev_live[k] = true;
+  assign_branches(b);
   b->graph_stale = true;
+  b->plan_uses = 0;
   b->dirty = false;
   return MPC_OK;
 }
@@ -312,12 +351,25 @@ mpc_status refresh(mpc_batch b) {
 // group (their claim counters zeroed first), then the closing of every member's step
 cudaError_t launch_batch_step(mpc_batch b, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
-  for (const StepArgs& a : b->solo_args)
-    if (e == cudaSuccess) e = launch_step(a, s);
-  if (e == cudaSuccess && !b->groups.empty())
-    e = cudaMemsetAsync(b->counters, 0, sizeof(uint32_t) * b->groups.size(), s);
-  for (const mpc_batch_s::Group& G : b->groups)
-    if (e == cudaSuccess) e = launch_step_packed(G.table, G.variant, b->det, G.grid, G.smem, s);
+  const int nb = b->n_branches;
+  if (!b->groups.empty()) e = cudaMemsetAsync(b->counters, 0, sizeof(uint32_t) * b->groups.size(), s);
+  if (e == cudaSuccess && nb > 1) {
+    e = cudaEventRecord(b->fork_ev, s);
+    for (int k = 0; k < nb && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->branch[k], b->fork_ev, 0);
+  }
+  auto on = [&](size_t unit) { return nb > 1 ? b->branch[b->unit_branch[unit]] : s; };
+  for (size_t i = 0; i < b->solo_args.size() && e == cudaSuccess; ++i)
+    e = launch_step(b->solo_args[i], on(i));
+  for (size_t i = 0; i < b->groups.size() && e == cudaSuccess; ++i) {
+    const mpc_batch_s::Group& G = b->groups[i];
+    e = launch_step_packed(G.table, G.variant, b->det, G.grid, G.smem, on(b->solo_args.size() + i));
+  }
+  if (e == cudaSuccess && nb > 1) {
+    for (int k = 0; k < nb && e == cudaSuccess; ++k) {
+      e = cudaEventRecord(b->join_ev[k], b->branch[k]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->join_ev[k], 0);
+    }
+  }
   if (e == cudaSuccess) e = launch_advance_batch(b->table_dev, b->adv_grid, s);
   return e;
 }
@@ -444,6 +496,11 @@ mpc_status mpc_batch_destroy(mpc_batch b) {
   if (b->ctrl_slab) cudaFreeHost(b->ctrl_slab);
   if (b->adm_stream) cudaStreamDestroy(b->adm_stream);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  for (int k = 0; k < kBranches; ++k) {
+    if (b->branch[k]) cudaStreamDestroy(b->branch[k]);
+    if (b->join_ev[k]) cudaEventDestroy(b->join_ev[k]);
+  }
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
   delete b;
   return MPC_OK;
 }
@@ -479,8 +536,13 @@ mpc_status mpc_batch_create(const mpc_batch_config* cfg, void* stream, mpc_batch
   b->adv_grid = b->num_sms;
   b->solo_bricks = kSoloWaves * kWaveCtasPerSm * b->num_sms;
   if (cudaStreamCreateWithFlags(&b->adm_stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+      cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) != cudaSuccess)
     return bail(MPC_ECUDA, "stream creation failed");
+  for (int k = 0; k < kBranches; ++k)
+    if (cudaStreamCreateWithFlags(&b->branch[k], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->join_ev[k], cudaEventDisableTiming) != cudaSuccess)
+      return bail(MPC_ECUDA, "stream creation failed");
   if (cudaMallocHost(&b->ctrl_slab, sizeof(Ctrl) * (size_t)b->max_boxes) != cudaSuccess) {
     b->ctrl_slab = nullptr;
     return bail(MPC_ENOMEM, "pinned host allocation failed");
@@ -564,6 +626,7 @@ mpc_status mpc_batch_add(mpc_batch b, const mpc_params* p, mpc_handle* out) {
   b->slot_of[h] = slot;
   b->boxes.push_back(h);
   b->gens.push_back(h->buffers_gen);
+  b->stepping.push_back(1);
   b->dirty = true;
   *out = h;
   return MPC_OK;
@@ -575,6 +638,7 @@ mpc_status mpc_batch_remove(mpc_batch b, mpc_handle h) {
   if (!h || it == b->boxes.end()) return bfail(b, MPC_EINVAL, "not a member of this batch");
   BCU(b, cudaSetDevice(b->device));
   b->gens.erase(b->gens.begin() + (it - b->boxes.begin()));
+  b->stepping.erase(b->stepping.begin() + (it - b->boxes.begin()));
   b->boxes.erase(it);
   const int slot = b->slot_of[h];
   b->slot_of.erase(h);
@@ -592,11 +656,17 @@ mpc_status mpc_batch_step(mpc_batch b, int64_t nsteps) {
   if (nsteps < 0) return bfail(b, MPC_EINVAL, "nsteps must be >= 0");
   BCU(b, cudaSetDevice(b->device));
   if (nsteps == 0 || b->boxes.empty()) return MPC_OK;
+  const auto t_plan = std::chrono::steady_clock::now();
   if (mpc_status st = refresh(b); st != MPC_OK) return st;
   for (mpc_handle h : b->boxes) h->target_step += std::min(nsteps, h->limit - h->target_step);
   int64_t n = nsteps;
-  if (n >= b->graph_steps) {
+  // a plan used once (e.g. between admissions of a serving loop) is launched directly;
+  // from its second use on it is captured
+  const bool graphed = n >= b->graph_steps && b->plan_uses++ >= 1;
+  if (graphed)
     if (mpc_status st = build_graph(b); st != MPC_OK) return st;
+  b->plan_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_plan).count();
+  if (graphed) {
     for (; n >= b->graph_steps; n -= b->graph_steps) BCU(b, cudaGraphLaunch(b->graph, b->stream));
   }
   for (; n > 0; --n) BCU(b, launch_batch_step(b, b->stream));
@@ -639,6 +709,7 @@ mpc_status mpc_batch_get_info(mpc_batch b, mpc_batch_info* out) {
     out->smem_bytes = std::max(out->smem_bytes, (int32_t)G.smem);
   }
   out->packed_launches = (int32_t)b->groups.size();
+  out->plan_ms = (float)b->plan_ms;
   out->graph_builds = b->graph_builds;
   out->tuned_classes = (int32_t)b->tuned.size();
   out->solo_boxes = (int32_t)b->solo_args.size();

@@ -3,8 +3,10 @@
 // Jobs wait in arrival order.  Between chunks of steps the loop admits every job that
 // has arrived and fits the HBM budget (the batch arena), retires jobs that reached their
 // step count (their observables become a Green-Kubo viscosity, their memory returns to
-// the arena once the queued work is past it), and enqueues the next chunk, sized so that
-// the next job to finish ends on the chunk boundary.  While a chunk runs, the loop keeps
+// the arena once the queued work is past it), picks the resident jobs that step in the
+// next chunk (by default the least remaining work first, or the oldest first, until the
+// GPU is full; the others hold through their step limits), and enqueues the chunk, sized
+// so that the next stepping job to finish ends on the chunk boundary.  While a chunk runs, the loop keeps
 // admitting arrivals: box creation runs on the batch's side stream and overlaps the
 // chunk, and the new members join the next chunk.
 #include <algorithm>
@@ -27,6 +29,12 @@ namespace {
 
 thread_local std::string g_server_create_error;
 
+// default particles the stepping jobs of a chunk should hold: about twenty waves of
+// 640-particle bricks on 152 SMs at five CTAs each, so that several jobs step together
+// and the last partial wave of one launch overlaps the next (measured on the serving
+// trace: 1M-particle fills leave the GPU waiting on launch tails, 16M recover them)
+constexpr int64_t kFillParticles = 16000000;
+
 struct Job {
   mpc_job spec{};
   mpc_job_result res{};
@@ -46,14 +54,18 @@ struct mpc_server_s {
   mpc_server_config cfg{};
   cudaStream_t stream = nullptr;
   cudaStream_t side = nullptr;  // result copies that must not wait for queued chunks
-  bool det = false, sequential = false;
+  bool det = false, sequential = false, share_all = false, first_come = false;
+  int64_t fill = kFillParticles;
   int chunk = 100;
   mpc_batch batch = nullptr;
   std::vector<Job> jobs;
   size_t next_queued = 0;  // jobs before this index are admitted, done or failed
   bool started = false;
   std::chrono::steady_clock::time_point t0;
-  cudaEvent_t chunk_done = nullptr;
+  cudaEvent_t chunk_start = nullptr, chunk_done = nullptr;
+  mpc_server_stats stats{};
+  bool gap_open = false;
+  double gap_from = 0.0;
   std::string err;
 };
 
@@ -211,22 +223,50 @@ mpc_status run_batched(mpc_server s, double deadline) {
       for (Job* j : fetched) analyse(s, *j);
       return sfail(s, MPC_ETIMEOUT, "server run timed out");
     }
-    int64_t min_left = INT64_MAX;
-    for (const Job& j : s->jobs)  // resident jobs (retired ones await analysis, h = NULL)
-      if (j.res.status == MPC_JOB_RUNNING && j.h) min_left = std::min(min_left, j.spec.steps - j.h->target_step);
+    // the jobs that step in this chunk: all resident jobs, or (default) those with the
+    // least remaining work -- or the oldest -- until they fill the GPU; the others hold
+    // at their step
+    std::vector<Job*> resident;  // (retired jobs await analysis with h = NULL)
+    for (Job& j : s->jobs)
+      if (j.res.status == MPC_JOB_RUNNING && j.h) resident.push_back(&j);
+    if (!s->first_come)
+      std::stable_sort(resident.begin(), resident.end(), [](const Job* a, const Job* b) {
+        const double wa = (double)(a->spec.steps - a->h->target_step) * (double)a->h->N;
+        const double wb = (double)(b->spec.steps - b->h->target_step) * (double)b->h->N;
+        return wa < wb;
+      });  // else arrival order (jobs are kept in arrival order)
+    int64_t min_left = INT64_MAX, filled = 0;
+    for (Job* j : resident) {
+      const bool step = s->share_all || filled < s->fill;
+      const int64_t want = step ? j->spec.steps : j->h->target_step;
+      if (j->h->limit != want) {
+        if (mpc_status st = mpc_set_step_limit(j->h, want); st != MPC_OK)
+          return sfail(s, st, "step limit: " + j->h->err);
+      }
+      if (step) {
+        filled += j->h->N;
+        min_left = std::min(min_left, j->spec.steps - j->h->target_step);
+      }
+    }
     const bool launched = min_left != INT64_MAX;
     if (launched) {
       // the next chunk ends where the first resident job finishes (at most chunk steps)
       const int64_t n = std::max<int64_t>(1, std::min<int64_t>(min_left, s->chunk));
+      if (cudaEventRecord(s->chunk_start, s->stream) != cudaSuccess)
+        return sfail(s, MPC_ECUDA, "event record failed");
       if (mpc_status st = mpc_batch_step(s->batch, n); st != MPC_OK)
         return sfail(s, st, std::string("batch step: ") + mpc_batch_last_error(s->batch));
       if (cudaEventRecord(s->chunk_done, s->stream) != cudaSuccess)
         return sfail(s, MPC_ECUDA, "event record failed");
+      if (s->gap_open) s->stats.host_gap_ms += 1e3 * (now_s(s->t0) - s->gap_from);
+      s->stats.chunks += 1;
+      s->stats.chunk_steps += n;
     }
     // while the chunk runs: analyse the jobs retired after the previous chunk
     for (Job* j : fetched) analyse(s, *j);
     fetched.clear();
     if (!launched) {
+      s->gap_open = false;  // idle for lack of work, not for the host
       // nothing resident: wait for the next arrival
       double next = 1e300;
       for (size_t i = s->next_queued; i < s->jobs.size(); ++i)
@@ -241,6 +281,13 @@ mpc_status run_batched(mpc_server s, double deadline) {
       std::this_thread::sleep_for(std::chrono::microseconds(200));
     }
     cudaGetLastError();
+    s->gap_open = true;  // the GPU is idle from here until the next chunk is enqueued
+    s->gap_from = now_s(s->t0);
+    {
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, s->chunk_start, s->chunk_done) == cudaSuccess) s->stats.gpu_ms += ms;
+      else cudaGetLastError();
+    }
     if (mpc_status st = mpc_batch_synchronize(s->batch); st != MPC_OK)
       return sfail(s, st, std::string("batch: ") + mpc_batch_last_error(s->batch));
     for (Job& j : s->jobs) {
@@ -297,6 +344,7 @@ mpc_status mpc_server_destroy(mpc_server s) {
   if (!s) return MPC_OK;
   if (s->batch) mpc_batch_destroy(s->batch);
   if (s->chunk_done) cudaEventDestroy(s->chunk_done);
+  if (s->chunk_start) cudaEventDestroy(s->chunk_start);
   if (s->side) cudaStreamDestroy(s->side);
   delete s;
   return MPC_OK;
@@ -306,8 +354,9 @@ mpc_status mpc_server_create(const mpc_server_config* cfg, void* stream, mpc_ser
   if (!cfg || !out) return sfail(nullptr, MPC_EINVAL, "config and out are required");
   *out = nullptr;
   if (cfg->hbm_budget_bytes == 0 || cfg->chunk_steps < 0 || cfg->max_active < 0 ||
-      cfg->max_active > kMaxBatchBoxes || cfg->reserved != 0 ||
-      (cfg->flags & ~(uint32_t)(MPC_SERVER_DETERMINISTIC | MPC_SERVER_SEQUENTIAL)))
+      cfg->max_active > kMaxBatchBoxes || cfg->fill_kparticles < 0 ||
+      (cfg->flags & ~(uint32_t)(MPC_SERVER_DETERMINISTIC | MPC_SERVER_SEQUENTIAL |
+                                MPC_SERVER_SHARE_ALL | MPC_SERVER_FIRST_COME)))
     return sfail(nullptr, MPC_EINVAL, "invalid server configuration");
   mpc_server s = new (std::nothrow) mpc_server_s();
   if (!s) return sfail(nullptr, MPC_ENOMEM, "host allocation failed");
@@ -315,8 +364,11 @@ mpc_status mpc_server_create(const mpc_server_config* cfg, void* stream, mpc_ser
   s->stream = static_cast<cudaStream_t>(stream);
   s->det = (cfg->flags & MPC_SERVER_DETERMINISTIC) != 0;
   s->sequential = (cfg->flags & MPC_SERVER_SEQUENTIAL) != 0;
+  s->share_all = (cfg->flags & MPC_SERVER_SHARE_ALL) != 0;
+  s->first_come = (cfg->flags & MPC_SERVER_FIRST_COME) != 0;
+  if (cfg->fill_kparticles > 0) s->fill = (int64_t)cfg->fill_kparticles * 1000;
   s->chunk = cfg->chunk_steps > 0 ? cfg->chunk_steps : 100;
-  if (cudaEventCreateWithFlags(&s->chunk_done, cudaEventDisableTiming) != cudaSuccess ||
+  if (cudaEventCreate(&s->chunk_done) != cudaSuccess || cudaEventCreate(&s->chunk_start) != cudaSuccess ||
       cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     mpc_server_destroy(s);
@@ -365,6 +417,20 @@ mpc_status mpc_server_run(mpc_server s, double timeout_s) {
   }
   const double deadline = now_s(s->t0) + (timeout_s > 0 ? timeout_s : 1e300);
   return s->sequential ? run_sequential(s, deadline) : run_batched(s, deadline);
+}
+
+mpc_status mpc_server_get_stats(mpc_server s, mpc_server_stats* out) {
+  if (!s) return sfail(nullptr, MPC_EINVAL, "server is NULL");
+  if (!out) return sfail(s, MPC_EINVAL, "out is NULL");
+  *out = s->stats;
+  if (s->batch) {
+    mpc_batch_info bi{};
+    if (mpc_batch_get_info(s->batch, &bi) == MPC_OK) {
+      out->plan_ms = bi.plan_ms;
+      out->graph_builds = bi.graph_builds;
+    }
+  }
+  return MPC_OK;
 }
 
 mpc_status mpc_server_job(mpc_server s, int64_t job_id, mpc_job_result* out) {

@@ -53,6 +53,7 @@ LAYOUT = [
     ("offsetof(mpc_batch_info, solo_boxes)", lambda: mpc.mpc_batch_info.solo_boxes.offset),
     ("offsetof(mpc_batch_info, packed_launches)",
      lambda: mpc.mpc_batch_info.packed_launches.offset),
+    ("offsetof(mpc_batch_info, plan_ms)", lambda: mpc.mpc_batch_info.plan_ms.offset),
     ("sizeof(mpc_server_config)", lambda: ctypes.sizeof(mpc.mpc_server_config)),
     ("sizeof(mpc_job)", lambda: ctypes.sizeof(mpc.mpc_job)),
     ("sizeof(mpc_job_result)", lambda: ctypes.sizeof(mpc.mpc_job_result)),
@@ -60,6 +61,10 @@ LAYOUT = [
     ("offsetof(mpc_job, keep)", lambda: mpc.mpc_job.keep.offset),
     ("offsetof(mpc_job_result, eta_gk)", lambda: mpc.mpc_job_result.eta_gk.offset),
     ("offsetof(mpc_server_config, flags)", lambda: mpc.mpc_server_config.flags.offset),
+    ("offsetof(mpc_server_config, fill_kparticles)",
+     lambda: mpc.mpc_server_config.fill_kparticles.offset),
+    ("sizeof(mpc_server_stats)", lambda: ctypes.sizeof(mpc.mpc_server_stats)),
+    ("offsetof(mpc_server_stats, plan_ms)", lambda: mpc.mpc_server_stats.plan_ms.offset),
 ]
 
 
