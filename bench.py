@@ -327,6 +327,7 @@ def run_batched(args, mpc, torch) -> dict:
     ms_plain = e0.elapsed_time(e1)
     for s_ in sims:
         s_.close()
+    torch.cuda.empty_cache()
     jobs_steps = 10000
     return {
         "workload": f"{len(boxes)} periodic boxes, L in {{8,12,...,64}}, N_c in {{5,10,20}}, "
@@ -528,6 +529,7 @@ def run_ours(args):
                 "frac_two_sweep_72B_model": value / world * TWO_SWEEP_MODEL_BYTES / 1e9 / peak}
 
     sim.close()
+    torch.cuda.empty_cache()  # the box's memory came from torch's caching allocator
     batched = None
     if rank == 0 and world == 1 and not args.no_batch:
         batched = run_batched(args, mpc, torch)
