@@ -208,6 +208,26 @@ mpc_status mpc_sort_by_cell_noalloc(const int32_t L[3], int64_t n, const uint32_
                                     const float* V, const uint32_t* id, uint32_t* X_out,
                                     float* V_out, uint32_t* id_out, void* stream);
 
+/* Checkpoint files (Sec. III.G.2, "Input/Output"): parameters and the step count in a
+ * text file `<prefix>.txt` (one "key = value" per line), all particle data in binary in
+ * `<prefix>.particles` -- x[N], y[N], z[N] (u32 fixed point, the state contract), vx[N],
+ * vy[N], vz[N] (f32), id[N] (u32), ordered by unshifted cell index -- and per unshifted
+ * cell its particle count and the offset of its first particle in `<prefix>.cells`
+ * (u32 count[C], then u32 offset[C], or u64 offsets when N >= 2^32; C = Lx Ly Lz), all
+ * little-endian.  The paper also stores a random seed per cell; here random numbers are
+ * counter-based (Philox keyed by the run's seed, the step and the cell), so the seed in
+ * the text file is all a reader needs.  Writing synchronises the handle's stream and
+ * needs 32 B of host memory per particle; returns MPC_EINVAL when a file cannot be
+ * written. */
+mpc_status mpc_checkpoint_write(mpc_handle h, const char* prefix);
+
+/* Create a box from a checkpoint written by mpc_checkpoint_write (parameters, step count
+ * and state), on `stream` with `alloc` as in mpc_create.  MPC_EINVAL for a missing,
+ * malformed or inconsistent file set (counts that do not match the particles' cells,
+ * positions outside the box, unknown format version). */
+mpc_status mpc_checkpoint_read(const char* prefix, void* stream, const mpc_allocator* alloc,
+                               mpc_handle* out);
+
 /* Stop the box at step `limit`: later steps (single or batched) leave it unchanged.
  * limit must not lie before the steps already requested (MPC_EINVAL).  Asynchronous.
  * The paper runs one system per job and has no counterpart; batches and the serving

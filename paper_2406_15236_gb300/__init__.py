@@ -152,6 +152,8 @@ def lib():
     L.mpc_sort_by_cell_noalloc.argtypes = [P(ctypes.c_int32), ctypes.c_int64, vp, vp, vp, vp, vp,
                                            vp, vp]
     L.mpc_set_step_limit.argtypes = [vp, ctypes.c_int64]
+    L.mpc_checkpoint_write.argtypes = [vp, ctypes.c_char_p]
+    L.mpc_checkpoint_read.argtypes = [ctypes.c_char_p, vp, P(mpc_allocator), P(vp)]
     L.mpc_footprint.argtypes = [P(mpc_params), P(ctypes.c_uint64), P(ctypes.c_uint64)]
     L.mpc_autotune.argtypes = [P(mpc_params), vp, ctypes.c_uint64, P(ctypes.c_int32),
                                P(ctypes.c_int32), P(ctypes.c_double)]
@@ -181,6 +183,7 @@ def lib():
                  "mpc_set_state", "mpc_get_cell_counts", "mpc_observables",
                  "mpc_observable_series", "mpc_get_info", "mpc_set_profiling",
                  "mpc_profile_step_kernel", "mpc_sort_by_cell_noalloc", "mpc_set_step_limit",
+                 "mpc_checkpoint_write", "mpc_checkpoint_read",
                  "mpc_footprint", "mpc_autotune", "mpc_batch_create", "mpc_batch_destroy",
                  "mpc_batch_add", "mpc_batch_remove", "mpc_batch_step", "mpc_batch_synchronize",
                  "mpc_batch_get_info", "mpc_server_create", "mpc_server_destroy",
@@ -348,6 +351,18 @@ def mpc_sort_by_cell_noalloc(L, n, X, V, ids, X_out, V_out, ids_out, stream=None
                                           _addr(V_out), _addr(ids_out), ctypes.c_void_p(stream or 0)))
 
 
+def mpc_checkpoint_write(handle, prefix: str) -> None:
+    _check(lib().mpc_checkpoint_write(handle, os.fsencode(prefix)), handle)
+
+
+def mpc_checkpoint_read(prefix: str, stream=None, allocator: mpc_allocator | None = None):
+    h = ctypes.c_void_p()
+    _check(lib().mpc_checkpoint_read(os.fsencode(prefix), ctypes.c_void_p(stream or 0),
+                                     ctypes.byref(allocator) if allocator is not None else None,
+                                     ctypes.byref(h)))
+    return h
+
+
 def mpc_set_step_limit(handle, limit: int) -> None:
     _check(lib().mpc_set_step_limit(handle, int(limit)), handle)
 
@@ -476,6 +491,10 @@ class Box:
     def set_step_limit(self, limit: int):
         mpc_set_step_limit(self.handle, limit)
 
+    def checkpoint(self, prefix: str):
+        """Write <prefix>.txt / .particles / .cells (Sec. III.G.2 checkpoint layout)."""
+        mpc_checkpoint_write(self.handle, prefix)
+
     def get_state(self, cells=False):
         """(X (3,N) uint32, V (3,N) float32, ids (N,), step[, cell]) on the host, sorted by
         unshifted cell."""
@@ -523,6 +542,20 @@ class Simulation(Box):
         self.stream = stream
         self._alloc = torch_allocator() if use_torch_allocator else None
         super().__init__(mpc_create(params, stream, self._alloc), params)
+
+    @classmethod
+    def from_checkpoint(cls, prefix: str, stream=None, use_torch_allocator=True):
+        """A box restored from a checkpoint written by `checkpoint`."""
+        import torch
+
+        self = cls.__new__(cls)
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        self._alloc = torch_allocator() if use_torch_allocator else None
+        h = mpc_checkpoint_read(prefix, stream, self._alloc)
+        Box.__init__(self, h, None)
+        return self
 
     def close(self):
         if self.handle is not None:
