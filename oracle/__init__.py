@@ -49,11 +49,16 @@ class Params(ctypes.Structure):
                 ("alpha_deg", ctypes.c_double), ("kT", ctypes.c_double), ("m", ctypes.c_double),
                 ("variant", ctypes.c_int32), ("thermostat", ctypes.c_int32),
                 ("walls_z", ctypes.c_int32), ("g", ctypes.c_double * 3),
-                ("seed", ctypes.c_uint64), ("box", ctypes.c_uint32)]
+                ("seed", ctypes.c_uint64), ("box", ctypes.c_uint32),
+                ("wall_u", ctypes.c_double * 2)]
+
+
+NO_SLIP, SLIP = 1, 2
 
 
 def params(L=(16, 16, 16), n_c=10.0, h=0.1, alpha_deg=130.0, kT=1.0, m=1.0, variant=SRD,
-           thermostat=0, walls_z=0, g=(0.0, 0.0, 0.0), seed=1, box=0) -> Params:
+           thermostat=0, walls_z=0, g=(0.0, 0.0, 0.0), seed=1, box=0,
+           wall_u=(0.0, 0.0)) -> Params:
     if isinstance(L, int):
         L = (L, L, L)
     p = Params()
@@ -62,6 +67,7 @@ def params(L=(16, 16, 16), n_c=10.0, h=0.1, alpha_deg=130.0, kT=1.0, m=1.0, vari
     p.variant, p.thermostat, p.walls_z = variant, thermostat, walls_z
     p.g[:] = list(g)
     p.seed, p.box = seed, box
+    p.wall_u[:] = list(wall_u)
     return p
 
 

@@ -227,10 +227,18 @@ static geom_t make_geom(const orc_params* p) {
 }
 
 /* Streaming, Eq. (1): kick by gravity ("External fields"), move ballistically, and
- * apply the boundary conditions ("Boundary conditions"): periodic wrap, or bounce-back
- * at the z walls -- the particle is reflected back into the box for the remainder of
- * the step and its whole velocity is reversed.  x: fixed-point position (in/out);
- * v: velocity (in: pre-kick; out: the velocity that enters the collision). */
+ * apply the boundary conditions ("Boundary conditions"): periodic wrap; or, at the z
+ * walls, no-slip bounce-back -- the particle is reflected back into the box for the
+ * remainder of the step and its velocity relative to the wall is reversed (a wall
+ * moving with u along x: v -> 2u - v) -- or slip (specular reflection: only v_z flips,
+ * the tangential motion continues).  x: fixed-point position (in/out); v: velocity (in:
+ * pre-kick; out: the velocity that enters the collision).
+ *
+ * Bounce-back positions in fixed point: the walls sit at w = -1/2 and P - 1/2, the z
+ * position is mirrored about the wall, and with tau the fraction of the step before the
+ * hit the lateral displacement is dx (2 tau - 1) + 2 U (1 - tau), U the wall's own
+ * displacement over a step; with 2 tau - 1 = (Z' - Z)/dz and 2(1 - tau) = (2 z_n - 2w)/dz
+ * this is the exact rational (dx (Z' - Z) + U (2 z_n - 2w)) / dz, rounded half to even. */
 static void stream_particle(const orc_params* p, const geom_t* g, uint32_t x[3], double v[3]) {
   double vk[3];
   int64_t d[3];
@@ -238,17 +246,19 @@ static void stream_particle(const orc_params* p, const geom_t* g, uint32_t x[3],
     vk[ax] = v[ax] + (double)g->gh[ax];
     d[ax] = displacement(vk[ax], g->hs, g->P[ax]);
   }
-  int crossed = 0;
+  int crossed = 0, top = 0;
   if (p->walls_z) {
     int64_t Z = (int64_t)x[2];
     int64_t zn = Z + d[2];
     int64_t Pz = (int64_t)g->P[2];
     int64_t Znew = zn;
-    if (zn >= Pz) { Znew = 2 * Pz - 1 - zn; crossed = 1; }
+    if (zn >= Pz) { Znew = 2 * Pz - 1 - zn; crossed = 1; top = 1; }
     else if (zn < 0) { Znew = -1 - zn; crossed = 1; }
-    if (crossed) {
-      /* lateral displacement scaled by the net over the free z displacement */
-      for (int ax = 0; ax < 2; ++ax) d[ax] = div_round_half_even(d[ax] * (Znew - Z), d[2]);
+    if (crossed && p->walls_z == 1) {
+      const int64_t U = displacement(p->wall_u[top], g->hs, g->P[0]);
+      const int64_t two_w = top ? 2 * Pz - 1 : -1;
+      d[0] = div_round_half_even(d[0] * (Znew - Z) + U * (2 * zn - two_w), d[2]);
+      d[1] = div_round_half_even(d[1] * (Znew - Z), d[2]);
     }
     x[2] = (uint32_t)Znew;
   } else {
@@ -256,7 +266,14 @@ static void stream_particle(const orc_params* p, const geom_t* g, uint32_t x[3],
   }
   x[0] = wrap_periodic((int64_t)x[0] + d[0], g->P[0]);
   x[1] = wrap_periodic((int64_t)x[1] + d[1], g->P[1]);
-  for (int ax = 0; ax < 3; ++ax) v[ax] = crossed ? -vk[ax] : vk[ax];
+  for (int ax = 0; ax < 3; ++ax) v[ax] = vk[ax];
+  if (crossed && p->walls_z == 2) {
+    v[2] = -vk[2];
+  } else if (crossed) {
+    v[0] = 2.0 * p->wall_u[top] - vk[0];
+    v[1] = -vk[1];
+    v[2] = -vk[2];
+  }
 }
 
 void orc_stream_one(const orc_params* p, uint32_t x[3], double v[3]) {
@@ -491,7 +508,7 @@ int orc_step(const orc_params* p, int64_t N, uint32_t* X, double* V, const uint3
     if (p->variant == ORC_SRD) {
       /* phantom particles in the wall part of cut cells (Sec. II, Boundary conditions) */
       double nph = 0.0, Pph[3] = {0, 0, 0}, Kint = 0.0;
-      if (p->walls_z) {
+      if (p->walls_z == 1) {
         int64_t cz = c / ((int64_t)p->L[0] * p->L[1]);
         double s = (double)S[2] * g.inv2F;
         double phi = -1.0;
@@ -509,7 +526,8 @@ int orc_step(const orc_params* p, int64_t N, uint32_t* X, double* V, const uint3
           box_muller(uniform01(r[1]), uniform01(r[2]), &zx, &zy);
           box_muller(uniform01(r1[0]), uniform01(r1[1]), &zz, &zdummy);
           double sp = m * sqrt(nph * p->kT / m);
-          Pph[0] = sp * zx;
+          /* phantoms move with their wall on average */
+          Pph[0] = sp * zx + m * nph * p->wall_u[cz == 0 ? 0 : 1];
           Pph[1] = sp * zy;
           Pph[2] = sp * zz;
           if (k >= 2) {

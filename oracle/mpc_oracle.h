@@ -33,10 +33,12 @@ typedef struct {
   double m;              /* particle mass */
   int32_t variant;       /* ORC_SRD / ORC_AT_A / ORC_SRD_A */
   int32_t thermostat;    /* 1: MBS after SRD */
-  int32_t walls_z;       /* 1: no-slip bounce-back walls at z = 0 and z = Lz */
+  int32_t walls_z;       /* walls at z = 0 and z = Lz: 0 none (periodic), 1 no-slip
+                            (bounce-back + phantom particles), 2 slip (specular) */
   double g[3];           /* body-force acceleration */
   uint64_t seed;
   uint32_t box;          /* fourth Philox counter word */
+  double wall_u[2];      /* x velocity of the no-slip wall at z = 0 and at z = Lz */
 } orc_params;
 
 /* per-cell flags written by orc_step */
