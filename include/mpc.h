@@ -84,7 +84,9 @@ typedef struct {
   double m;              /* particle mass, > 0 */
   int32_t variant;       /* mpc_variant */
   int32_t thermostat;    /* 1: MBS thermostat after the collision (MPC_SRD only) */
-  int32_t walls_z;       /* 0: periodic in z; 1: no-slip walls at z = 0 and z = Lz */
+  int32_t walls_z;       /* walls at z = 0 and z = Lz (Sec. II, Boundary conditions):
+                            0 none (periodic in z); 1 no-slip (bounce-back, phantom
+                            particles in cut cells); 2 slip (specular reflection) */
   double gravity[3];     /* body-force acceleration g */
   uint64_t seed;         /* Philox key */
   uint32_t box_id;       /* Philox counter word 3 (distinguishes boxes with one seed) */
@@ -97,6 +99,8 @@ typedef struct {
                                <= 32; see mpc_autotune */
   int32_t obs_ring;         /* rows of the per-step observables ring; 0 = 1024 */
   int32_t reserved;         /* must be 0 */
+  double wall_u[2];         /* x velocity of the no-slip walls at z = 0 and z = Lz (shear
+                               flow between moving walls); 0 unless walls_z = 1 */
 } mpc_params;
 
 /* Device-memory provider.  alloc returns device memory of `bytes` (>= 256-byte aligned)

@@ -20,6 +20,7 @@ from . import _build
 _LIB_PATH = _build.LIB
 
 MPC_SRD, MPC_AT_A, MPC_SRD_A = 0, 1, 2
+MPC_WALLS_NONE, MPC_WALLS_NO_SLIP, MPC_WALLS_SLIP = 0, 1, 2
 MPC_OK, MPC_EINVAL, MPC_ENOMEM, MPC_ECUDA, MPC_ETIMEOUT, MPC_ESTATE = range(6)
 MPC_FLAG_OBSERVABLES, MPC_FLAG_DEBUG_CELLS, MPC_FLAG_DETERMINISTIC = 1, 2, 4
 MPC_BATCH_DETERMINISTIC, MPC_BATCH_AUTOTUNE, MPC_BATCH_PACK_ALL = 1, 2, 4
@@ -44,7 +45,8 @@ class mpc_params(ctypes.Structure):
                 ("box_id", ctypes.c_uint32), ("flags", ctypes.c_uint32),
                 ("capacity", ctypes.c_int32), ("graph_steps", ctypes.c_int32),
                 ("tile_particles", ctypes.c_int32), ("threads_per_cell", ctypes.c_int32),
-                ("obs_ring", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("obs_ring", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("wall_u", ctypes.c_double * 2)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -215,7 +217,7 @@ def _check_batch(status, batch=None):
 def make_params(L=(16, 16, 16), n_c=10.0, h=0.1, alpha_deg=130.0, kT=1.0, m=1.0,
                 variant=MPC_SRD, thermostat=0, walls_z=0, gravity=(0.0, 0.0, 0.0), seed=1,
                 box_id=0, flags=0, capacity=0, graph_steps=0, tile_particles=0,
-                threads_per_cell=0, obs_ring=0) -> mpc_params:
+                threads_per_cell=0, obs_ring=0, wall_u=(0.0, 0.0)) -> mpc_params:
     if isinstance(L, int):
         L = (L, L, L)
     p = mpc_params()
@@ -228,6 +230,7 @@ def make_params(L=(16, 16, 16), n_c=10.0, h=0.1, alpha_deg=130.0, kT=1.0, m=1.0,
     p.capacity, p.graph_steps = capacity, graph_steps
     p.tile_particles, p.threads_per_cell, p.obs_ring = tile_particles, threads_per_cell, obs_ring
     p.reserved = 0
+    p.wall_u[:] = list(wall_u)
     return p
 
 

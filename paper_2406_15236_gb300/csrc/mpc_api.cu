@@ -132,8 +132,15 @@ mpc_status validate(const mpc_params* p) {
     return fail(nullptr, MPC_EINVAL, "variant must be MPC_SRD, MPC_AT_A or MPC_SRD_A");
   if (p->thermostat && p->variant != MPC_SRD)
     return fail(nullptr, MPC_EINVAL, "the MBS thermostat applies to SRD only");
+  if (p->walls_z < 0 || p->walls_z > 2)
+    return fail(nullptr, MPC_EINVAL, "walls_z must be 0 (periodic), 1 (no-slip) or 2 (slip)");
   if (p->walls_z && p->variant != MPC_SRD)
     return fail(nullptr, MPC_EINVAL, "walls are supported with SRD only");
+  for (int k = 0; k < 2; ++k) {
+    if (!std::isfinite(p->wall_u[k])) return fail(nullptr, MPC_EINVAL, "wall_u must be finite");
+    if (p->wall_u[k] != 0.0 && p->walls_z != 1)
+      return fail(nullptr, MPC_EINVAL, "moving walls need walls_z = 1 (no-slip)");
+  }
   for (int ax = 0; ax < 3; ++ax)
     if (!std::isfinite(p->gravity[ax])) return fail(nullptr, MPC_EINVAL, "gravity must be finite");
   const double vol = (double)p->L[0] * p->L[1] * p->L[2];
@@ -458,7 +465,9 @@ mpc_status plan_box(const mpc_params* p, size_t smem_limit, Geom& g, int64_t& N)
     g.P[ax] = (uint32_t)p->L[ax] << g.F;
     g.gh[ax] = (float)(p->gravity[ax] * p->h);
   }
-  g.walls = p->walls_z ? 1 : 0;
+  g.walls = p->walls_z;
+  g.wall_u[0] = (float)p->wall_u[0];
+  g.wall_u[1] = (float)p->wall_u[1];
   if (g.walls) g.Lc[2] += 1;
   g.hs = (float)std::ldexp(p->h, g.F);
   g.inv2F = (float)std::ldexp(1.0, -g.F);

@@ -88,10 +88,11 @@ mpc_status mpc_checkpoint_write(mpc_handle h, const char* prefix) {
         "format = mpc-checkpoint %d\nL = %d %d %d\na = %.17g\nn_c = %.17g\nh = %.17g\n"
         "alpha_deg = %.17g\nkT = %.17g\nm = %.17g\nvariant = %d\nthermostat = %d\nwalls_z = %d\n"
         "gravity = %.17g %.17g %.17g\nseed = %" PRIu64 "\nbox_id = %u\nflags = %u\nstep = %" PRId64
-        "\nn_particles = %" PRId64 "\nfixed_bits = %d\ncells = %" PRIu64 "\noffset_bytes = %d\n",
+        "\nn_particles = %" PRId64 "\nfixed_bits = %d\ncells = %" PRIu64 "\noffset_bytes = %d\n"
+        "wall_u = %.17g %.17g\n",
         kFormat, p.L[0], p.L[1], p.L[2], p.a, p.n_c, p.h, p.alpha_deg, p.kT, p.m, p.variant,
         p.thermostat, p.walls_z, p.gravity[0], p.gravity[1], p.gravity[2], p.seed, p.box_id, p.flags,
-        step, N, F, C, N >= (1LL << 32) ? 8 : 4);
+        step, N, F, C, N >= (1LL << 32) ? 8 : 4, p.wall_u[0], p.wall_u[1]);
     if (ok < 0) return fail(h, MPC_EINVAL, "cannot write " + base + ".txt");
   }
   {
@@ -172,6 +173,9 @@ mpc_status mpc_checkpoint_read(const char* prefix, void* stream, const mpc_alloc
             std::sscanf(kv["fixed_bits"].c_str(), "%d", &F) == 1 &&
             std::sscanf(kv["cells"].c_str(), "%" SCNu64, &C) == 1 &&
             std::sscanf(kv["offset_bytes"].c_str(), "%d", &off_bytes) == 1;
+  if (kv.count("wall_u") &&
+      std::sscanf(kv["wall_u"].c_str(), "%lf %lf", &p.wall_u[0], &p.wall_u[1]) != 2)
+    ok = false;
   if (!ok) return bad("malformed value in " + base + ".txt");
   for (int ax = 0; ax < 3; ++ax)
     if (p.L[ax] < 2 || p.L[ax] > 1024) return bad("L out of range");

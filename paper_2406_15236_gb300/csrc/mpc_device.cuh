@@ -131,9 +131,20 @@ __device__ __forceinline__ int64_t rdiv_half_even(int64_t num, int64_t den) {
 // streaming that produced them crossed a wall.
 constexpr uint32_t kCrossedBit = 0x80000000u;
 
+// Lateral displacement along x or y of a particle that bounced back from a no-slip wall
+// moving with displacement U per step along that axis (Sec. II, Boundary conditions):
+// with the walls at w = -1/2 and P - 1/2 and tau the fraction of the step before the
+// hit, d (2 tau - 1) + 2 U (1 - tau) = (d (Z' - Z) + U (2 z_n - 2w)) / dz exactly,
+// rounded half to even (Z' the mirrored, z_n the free end position).
+__device__ __forceinline__ int bounce_lateral(int d, int U, int64_t Z, int64_t zn, int64_t Znew,
+                                              int dz, int64_t two_w) {
+  return (int)rdiv_half_even((int64_t)d * (Znew - Z) + (int64_t)U * (2 * zn - two_w), (int64_t)dz);
+}
+
 // Eq. (1) with gravity kick and boundary conditions.  In: position x and velocity v
 // before the step.  Out: the streamed position (z with kCrossedBit set after a wall
-// hit).  The velocity entering the collision is (crossed ? -1 : 1) * (v + g h).
+// hit).  The velocity entering the collision is v + g h, reflected at a wall hit as
+// collision_velocity() says.
 __device__ __forceinline__ void stream(const Geom& g, uint32_t& x, uint32_t& y, uint32_t& z,
                                        float vx, float vy, float vz) {
   vx = __fadd_rn(vx, g.gh[0]);
@@ -147,9 +158,13 @@ __device__ __forceinline__ void stream(const Geom& g, uint32_t& x, uint32_t& y, 
     const int64_t zn = Z + dz;
     const int64_t Pz = g.P[2];
     if (zn >= Pz || zn < 0) {
-      const int64_t Znew = (zn >= Pz) ? (2 * Pz - 1 - zn) : (-1 - zn);
-      dx = (int)rdiv_half_even((int64_t)dx * (Znew - Z), (int64_t)dz);
-      dy = (int)rdiv_half_even((int64_t)dy * (Znew - Z), (int64_t)dz);
+      const bool top = zn >= Pz;
+      const int64_t Znew = top ? (2 * Pz - 1 - zn) : (-1 - zn);
+      if (g.walls == 1) {  // no-slip: bounce-back in the frame of the (moving) wall
+        const int64_t two_w = top ? 2 * Pz - 1 : -1;
+        dx = bounce_lateral(dx, displacement(g.wall_u[top], g.hs, g.P[0]), Z, zn, Znew, dz, two_w);
+        dy = bounce_lateral(dy, 0, Z, zn, Znew, dz, two_w);
+      }  // slip: specular reflection, the tangential motion continues
       z = (uint32_t)Znew | kCrossedBit;
     } else {
       z = (uint32_t)zn;
@@ -176,10 +191,14 @@ __device__ __forceinline__ void unstream(const Geom& g, uint32_t& x, uint32_t& y
   if (g.walls) {
     if (crossed) {
       const int64_t Pz = g.P[2];
-      const int64_t zn = (dz > 0) ? (2 * Pz - 1 - (int64_t)zs) : (-1 - (int64_t)zs);
+      const bool top = dz > 0;
+      const int64_t zn = top ? (2 * Pz - 1 - (int64_t)zs) : (-1 - (int64_t)zs);
       const int64_t Z = zn - dz;
-      dx = (int)rdiv_half_even((int64_t)dx * ((int64_t)zs - Z), (int64_t)dz);
-      dy = (int)rdiv_half_even((int64_t)dy * ((int64_t)zs - Z), (int64_t)dz);
+      if (g.walls == 1) {
+        const int64_t two_w = top ? 2 * Pz - 1 : -1;
+        dx = bounce_lateral(dx, displacement(g.wall_u[top], g.hs, g.P[0]), Z, zn, (int64_t)zs, dz, two_w);
+        dy = bounce_lateral(dy, 0, Z, zn, (int64_t)zs, dz, two_w);
+      }
       z = (uint32_t)Z;
     } else {
       z = zs - (uint32_t)dz;
@@ -191,16 +210,23 @@ __device__ __forceinline__ void unstream(const Geom& g, uint32_t& x, uint32_t& y
   y = add_wrap(y, -dy, g.P[1]);
 }
 
-// velocity entering the collision for a particle stored as (streamed x, pre-kick v)
+// velocity entering the collision for a particle stored as (streamed x, pre-kick v): the
+// kicked velocity, after a wall hit reflected -- specularly (slip: v_z flips) or in the
+// frame of the wall it hit (no-slip: v -> 2 u_wall - v)
 __device__ __forceinline__ void collision_velocity(const Geom& g, uint32_t zraw, float& vx, float& vy,
                                                    float& vz) {
   vx = __fadd_rn(vx, g.gh[0]);
   vy = __fadd_rn(vy, g.gh[1]);
   vz = __fadd_rn(vz, g.gh[2]);
   if (zraw & kCrossedBit) {
-    vx = -vx;
-    vy = -vy;
-    vz = -vz;
+    if (g.walls == 2) {
+      vz = -vz;
+    } else {
+      const bool top = vz > 0.0f;  // moving up before the hit: the wall at z = Lz
+      vx = 2.0f * g.wall_u[top] - vx;
+      vy = -vy;
+      vz = -vz;
+    }
   }
 }
 

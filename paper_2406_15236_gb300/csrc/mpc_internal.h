@@ -17,7 +17,8 @@ struct Geom {
   float hs;          // float32(h 2^F)
   float gh[3];       // float32(g h)
   float inv2F;       // 2^-F
-  int walls;         // no-slip walls at z = 0, Lz
+  int walls;         // walls at z = 0, Lz: 0 none, 1 no-slip, 2 slip
+  float wall_u[2];   // x velocity of the no-slip walls at z = 0 and z = Lz
   int B[3];          // cells per brick (powers of two)
   int Bs[3];         // log2 B
   int nb[3];         // bricks per axis

@@ -406,7 +406,7 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
         // (Sec. II, Boundary conditions): Poisson count, Gaussian total momentum, and
         // an internal kinetic energy ~ kT chi^2(3(n_ph - 1)); drawn by the group leader
         float nph = 0.f, Px = 0.f, Py = 0.f, Pz = 0.f, Kint = 0.f;
-        if (exists && n > 0 && sub == 0 && g.walls && (cz == 0 || cz == g.L[2])) {
+        if (exists && n > 0 && sub == 0 && g.walls == 1 && (cz == 0 || cz == g.L[2])) {
           const double sz_ = (double)S0z * (double)g.inv2F;
           const double phi = (cz == 0) ? sz_ : 1.0 - sz_;
           const uint4 r = draw(g, cg, step, kTagPhantom, 0u);
@@ -416,7 +416,9 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
           const float2 zxy = normal2(r.y, r.z);
           const float zz = normal2(r1.x, r1.y).x;
           const float sp = g.m * sqrtf(nph * g.kT / g.m);
-          Px = sp * zxy.x; Py = sp * zxy.y; Pz = sp * zz;
+          // phantoms move with their wall on average
+          Px = sp * zxy.x + g.m * nph * g.wall_u[cz == 0 ? 0 : 1];
+          Py = sp * zxy.y; Pz = sp * zz;
           if (k >= 2) Kint = g.kT * 2.0f * gamma_mt(g, cg, step, kTagPhGamma, 1.5f * (float)(k - 1));
         }
         if (tpc > 1) {

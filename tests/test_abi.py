@@ -45,6 +45,7 @@ LAYOUT = [
     ("offsetof(mpc_params, graph_steps)", lambda: mpc.mpc_params.graph_steps.offset),
     ("offsetof(mpc_params, tile_particles)", lambda: mpc.mpc_params.tile_particles.offset),
     ("offsetof(mpc_params, obs_ring)", lambda: mpc.mpc_params.obs_ring.offset),
+    ("offsetof(mpc_params, wall_u)", lambda: mpc.mpc_params.wall_u.offset),
     ("offsetof(mpc_obs, step)", lambda: mpc.mpc_obs.step.offset),
     ("offsetof(mpc_info, threads_per_cell)", lambda: mpc.mpc_info.threads_per_cell.offset),
     ("offsetof(mpc_batch_config, flags)", lambda: mpc.mpc_batch_config.flags.offset),
@@ -86,7 +87,10 @@ def test_struct_layouts_match_header(tmp_path):
                                  dict(gravity=(float("nan"), 0.0, 0.0)),
                                  dict(tile_particles=-1), dict(tile_particles=20000),
                                  dict(threads_per_cell=3), dict(threads_per_cell=64),
-                                 dict(obs_ring=-1), dict(flags=64)])
+                                 dict(obs_ring=-1), dict(flags=64), dict(walls_z=3),
+                                 dict(wall_u=(0.1, 0.0)),
+                                 dict(walls_z=2, wall_u=(0.0, -0.1)),
+                                 dict(walls_z=1, wall_u=(float("inf"), 0.0))])
 def test_invalid_parameters_rejected_without_device(bad):
     p = mpc.make_params(**bad)
     with pytest.raises(mpc.MpcError) as e:

@@ -74,3 +74,20 @@ def test_independently_written_checkpoint_is_read(tmp_path):
     par.check_step(par.oracle_params(L=L, n_c=n_c, h=0.1, alpha_deg=130.0, seed=9),
                    (X1, V1, id1), (X2, V2, id2), 5)
     sim.close()
+
+
+def test_checkpoint_keeps_moving_walls(tmp_path):
+    mpc = _mpc()
+    kw = dict(L=(6, 6, 8), n_c=8.0, h=0.1, alpha_deg=130.0, walls_z=1, thermostat=1,
+              wall_u=(-0.2, 0.35), seed=8, flags=mpc.MPC_FLAG_DETERMINISTIC)
+    sim = mpc.Simulation(**kw)
+    sim.step(9)
+    prefix = str(tmp_path / "walls")
+    sim.checkpoint(prefix)
+    rest = mpc.Simulation.from_checkpoint(prefix)
+    sim.step(6)
+    rest.step(6)
+    for a, b in zip(par.by_id(*sim.get_state()[:3]), par.by_id(*rest.get_state()[:3])):
+        np.testing.assert_array_equal(a, b)
+    sim.close()
+    rest.close()

@@ -1,0 +1,112 @@
+"""Slip walls (specular reflection) and moving no-slip walls (bounce-back in the wall
+frame, shear flow) on the GPU (Sec. II, Boundary conditions): per-step parity with the
+oracle, crafted wall hits, exact energy conservation with slip walls, and the linear
+Couette profile between walls moving in opposite directions."""
+import numpy as np
+import pytest
+
+from tests import _parity as par
+
+pytestmark = pytest.mark.gpu
+
+
+def _mpc():
+    import torch
+
+    import paper_2406_15236_gb300 as mpc
+
+    torch.cuda.set_device(0)
+    return mpc
+
+
+CASES = {
+    "slip": dict(L=(10, 8, 12), n_c=10.0, h=0.1, alpha_deg=130.0, walls_z=2, seed=51),
+    "slip_mbs_gravity": dict(L=(8, 8, 10), n_c=7.0, h=0.1, alpha_deg=130.0, walls_z=2,
+                             thermostat=1, gravity=(5e-3, 0.0, -2e-3), seed=52),
+    "couette": dict(L=(8, 6, 10), n_c=10.0, h=0.1, alpha_deg=130.0, walls_z=1, thermostat=1,
+                    wall_u=(-0.3, 0.3), seed=53),
+    "moving_one_wall_gravity": dict(L=(6, 6, 9), n_c=12.0, h=0.05, alpha_deg=90.0, walls_z=1,
+                                    wall_u=(0.0, 0.5), gravity=(0.0, 3e-3, 0.0), seed=54),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_walls_parity_every_step(name):
+    mpc = _mpc()
+    kw = dict(CASES[name], flags=mpc.MPC_FLAG_DEBUG_CELLS)
+    sim = mpc.Simulation(**kw)
+    p = par.oracle_params(**kw)
+    pre = sim.get_state()[:3]
+    for s in range(12):
+        sim.step(1)
+        X1, V1, id1, step, cell1 = sim.get_state(cells=True)
+        par.check_step(p, pre, (X1, V1, id1), s, post_cells=cell1, gpu_counts=sim.cell_counts())
+        pre = (X1, V1, id1)
+    sim.close()
+
+
+@pytest.mark.parametrize("walls,wall_u", [(2, (0.0, 0.0)), (1, (0.4, -0.25))])
+def test_crafted_wall_hits(walls, wall_u):
+    """Every particle starts within one step of a wall, moving into it."""
+    mpc = _mpc()
+    kw = dict(L=(6, 6, 8), n_c=6.0, h=0.1, alpha_deg=130.0, walls_z=walls, wall_u=wall_u,
+              seed=61, flags=mpc.MPC_FLAG_DEBUG_CELLS)
+    sim = mpc.Simulation(**kw)
+    X, V, ids, _ = sim.get_state()
+    F = sim.info.fixed_bits
+    rng = np.random.default_rng(3)
+    N = X.shape[1]
+    top = rng.random(N) < 0.5
+    dist = rng.uniform(0.0, 0.09, N)
+    X[2] = np.where(top, (8 - dist) * 2**F, dist * 2**F).astype(np.uint32)
+    speed = rng.uniform(0.5, 3.0, N)
+    V[2] = np.where(top, speed, -speed).astype(np.float32)
+    sim.set_state(X, V, ids, 0)
+    pre = sim.get_state()[:3]
+    p = par.oracle_params(**kw)
+    for s in range(3):
+        sim.step(1)
+        X1, V1, id1, step, cell1 = sim.get_state(cells=True)
+        par.check_step(p, pre, (X1, V1, id1), s, post_cells=cell1, gpu_counts=sim.cell_counts())
+        pre = (X1, V1, id1)
+    sim.close()
+
+
+def test_slip_walls_conserve_energy():
+    mpc = _mpc()
+    sim = mpc.Simulation(L=(16, 16, 20), n_c=10.0, h=0.1, alpha_deg=130.0, walls_z=2, seed=5,
+                         flags=mpc.MPC_FLAG_OBSERVABLES)
+    e0 = sim.observables()["ekin"]
+    sim.step(300)
+    rows = sim.observable_series(300)
+    e = 0.5 * rows[:, 3]
+    assert np.abs(e / e0 - 1).max() < 2e-5  # float32 rounding only
+    p = rows[:, 0:2]
+    assert np.abs(p).max() < 1e-4 * np.sqrt(2 * e0)  # tangential momentum stays zero
+    sim.close()
+
+
+def test_couette_profile_is_linear():
+    """Walls moving with -U/2 and +U/2 along x, MBS thermostat: v_x(z) = U (z/Lz - 1/2)."""
+    mpc = _mpc()
+    Lz, U = 20, 0.4
+    sim = mpc.Simulation(L=(24, 24, Lz), n_c=10.0, h=0.1, alpha_deg=130.0, walls_z=1,
+                         thermostat=1, wall_u=(-U / 2, U / 2), seed=77)
+    sim.step(3000)
+    F = sim.info.fixed_bits
+    nb = 20
+    prof, cnt = np.zeros(nb), np.zeros(nb)
+    for _ in range(20):
+        sim.step(50)
+        X, V, _, _ = sim.get_state()
+        b = np.minimum((X[2] / 2.0**F / Lz * nb).astype(int), nb - 1)
+        np.add.at(prof, b, V[0])
+        np.add.at(cnt, b, 1)
+    sim.close()
+    z = (np.arange(nb) + 0.5) * Lz / nb
+    v = prof / cnt
+    slope, icept = np.polyfit(z - Lz / 2, v, 1)
+    print(f"Couette slope {slope:.5f} (U/Lz {U / Lz:.5f}), intercept {icept:.2e}")
+    assert abs(slope - U / Lz) < 0.05 * U / Lz
+    assert abs(icept) < 0.01 * U
+    assert np.abs(v - (slope * (z - Lz / 2) + icept)).max() < 0.05 * U
