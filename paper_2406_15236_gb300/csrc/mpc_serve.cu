@@ -80,7 +80,8 @@ mpc_status sfail(mpc_server s, mpc_status st, const std::string& msg) {
 // Green-Kubo shear viscosity from per-step stress rows (Sec. II observables; the MPC
 // stress of the streaming and collision parts): eta = (V h / kT) [C(0)/2 + sum_{k=1..K}
 // C(k)], C the autocorrelation of each off-diagonal stress about its mean, averaged
-// over xy, yx, yz, zy, zx, xz; K = clamp(steps / 10, 20, 200).
+// over xy, yx, yz, zy, zx, xz; K = clamp(steps / 10, 10, 50): the MPC stress
+// decorrelates within a few steps, and longer windows only add noise.
 void green_kubo(const mpc_params& p, int64_t N, const double* rows, int64_t n, double& eta,
                 double& temp) {
   const double vol = (double)p.L[0] * p.L[1] * p.L[2];
@@ -95,7 +96,7 @@ void green_kubo(const mpc_params& p, int64_t N, const double* rows, int64_t n, d
   temp = n > 0 ? temp / (double)n : 0.0;
   eta = 0.0;
   if (n < 4) return;
-  const int64_t K = std::min<int64_t>(std::max<int64_t>(n / 10, 20), std::min<int64_t>(200, n - 1));
+  const int64_t K = std::min<int64_t>(std::max<int64_t>(n / 10, 10), std::min<int64_t>(50, n - 1));
   std::vector<double> sig((size_t)n);
   double acc = 0.0;
   for (int c = 0; c < 6; ++c) {
