@@ -52,10 +52,10 @@ struct Layout {
   size_t x, y, z, vx, vy, vz, id, gcell, ux, uy, uz, tag, perm, count, cstart, params, total;
 };
 
-__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
+__host__ __device__ constexpr size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
-__host__ __device__ inline Layout make_layout(int cap, int bc, int nparams, bool vran, int debug) {
-  Layout L;
+__host__ __device__ constexpr Layout make_layout(int cap, int bc, int nparams, bool vran, int debug) {
+  Layout L{};
   size_t o = 0;
   const size_t a4 = align16(size_t(cap) * 4);
   L.x = o; o += a4;
@@ -82,6 +82,36 @@ template <int VAR>
 __host__ __device__ inline Layout layout_for(const Geom& g) {
   return make_layout(g.cap, g.brick_cells, CellParams<VAR>::kParams,
                      CellParams<VAR>::kStoresRandomVelocity, g.debug);
+}
+
+// Brick geometries compiled in: the default ~640-particle tiles (capacity 864) of
+// 4x4x2, 4x4x4 and 8x4x4 cells.  With the shared-memory layout and the brick shape as
+// constants, array addresses and cell arithmetic fold into immediates (about 6 % faster
+// than reading them from the Geom).  TIER 0 takes everything from the Geom.
+template <int TIER>
+struct TierShape {
+  static constexpr int cap = 0, Bs0 = 0, Bs1 = 0, Bs2 = 0;
+};
+template <>
+struct TierShape<1> {
+  static constexpr int cap = 864, Bs0 = 2, Bs1 = 2, Bs2 = 1;
+};
+template <>
+struct TierShape<2> {
+  static constexpr int cap = 864, Bs0 = 2, Bs1 = 2, Bs2 = 2;
+};
+template <>
+struct TierShape<3> {
+  static constexpr int cap = 864, Bs0 = 3, Bs1 = 2, Bs2 = 2;
+};
+
+__host__ __device__ inline int tier_of(const Geom& g) {
+  if (g.cap != 864 || g.debug) return 0;
+  const int s0 = g.Bs[0], s1 = g.Bs[1], s2 = g.Bs[2];
+  if (s0 == 2 && s1 == 2 && s2 == 1) return 1;
+  if (s0 == 2 && s1 == 2 && s2 == 2) return 2;
+  if (s0 == 3 && s1 == 2 && s2 == 2) return 3;
+  return 0;
 }
 
 // --- small PTX wrappers -----------------------------------------------------------
@@ -199,11 +229,18 @@ struct BrickShared {
 // sh.bar once and tracks its phase (persistent kernels); otherwise the barrier is
 // initialised here and phase must be 0.  Returns false after a bounded wait gave up
 // (the CTA must stop).
-template <int VAR, bool DET, bool PERSIST>
+template <int VAR, bool DET, bool PERSIST, int TIER = 0>
 __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsigned char* smem,
                                            BrickShared& sh, uint32_t& phase) {
   const Geom& g = a.g;
-  const Layout lay = layout_for<VAR>(g);
+  using T = TierShape<TIER>;
+  // brick geometry: compile-time constants for TIER > 0, else from the Geom
+  const int cap = TIER ? T::cap : g.cap;
+  const int Bs0 = TIER ? T::Bs0 : g.Bs[0], Bs1 = TIER ? T::Bs1 : g.Bs[1], Bs2 = TIER ? T::Bs2 : g.Bs[2];
+  const int B0 = 1 << Bs0, B1 = 1 << Bs1, B2 = 1 << Bs2;
+  const Layout lay = TIER ? make_layout(T::cap, 1 << (T::Bs0 + T::Bs1 + T::Bs2), CellParams<VAR>::kParams,
+                                        CellParams<VAR>::kStoresRandomVelocity, 0)
+                          : layout_for<VAR>(g);
 
   uint32_t* sx = reinterpret_cast<uint32_t*>(smem + lay.x);
   uint32_t* sy = reinterpret_cast<uint32_t*>(smem + lay.y);
@@ -230,7 +267,7 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
 
   const int tid = threadIdx.x;
   const int lane = tid & 31;
-  const int bc = g.brick_cells;
+  const int bc = TIER ? (1 << (T::Bs0 + T::Bs1 + T::Bs2)) : g.brick_cells;
 
   // ---- 1. load the brick: thread 0 reads the step, its limit, the halt flag and both
   // count slots in one round trip, then starts the bulk copies ----
@@ -246,14 +283,14 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
     if (!skip) {
       const int p = (int)(st & 1);
       c = p ? c_odd : c_even;
-      if (c > (uint32_t)g.cap) c = g.cap;
+      if (c > (uint32_t)cap) c = cap;
       a.cnt[p][b] = 0;  // this buffer becomes the destination of the next step
       if (!PERSIST) mbar_init(&sh.bar, 1);
       const uint32_t bytes = (uint32_t)(((c + 3) & ~3u) * 4);
       mbar_expect_tx(&sh.bar, 7u * bytes);
       if (bytes) {
         const PBuf& sb = a.buf[p];
-        const size_t off = (size_t)b * g.cap;
+        const size_t off = (size_t)b * cap;
         bulk_g2s(sx, sb.x[0] + off, bytes, &sh.bar);
         bulk_g2s(sy, sb.x[1] + off, bytes, &sh.bar);
         bulk_g2s(sz, sb.x[2] + off, bytes, &sh.bar);
@@ -299,7 +336,7 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
   const int bx = b % g.nb[0];
   const int by = (b / g.nb[0]) % g.nb[1];
   const int bz = b / (g.nb[0] * g.nb[1]);
-  const int ox = bx << g.Bs[0], oy = by << g.Bs[1], oz = bz << g.Bs[2];
+  const int ox = bx << Bs0, oy = by << Bs1, oz = bz << Bs2;
 
   // ---- 2. rank each particle within its collision cell ----
   // Stored positions are already streamed for this step (the previous step streamed
@@ -314,9 +351,9 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
               cz = cell_axis(g, z, S0z, 2);
     const int lx = cx - ox, ly = cy - oy, lz = cz - oz;
     uint32_t lcr;
-    if ((unsigned)lx < (unsigned)g.B[0] && (unsigned)ly < (unsigned)g.B[1] &&
-        (unsigned)lz < (unsigned)g.B[2]) {
-      const uint32_t lc = (uint32_t)(lx | (ly << g.Bs[0]) | (lz << (g.Bs[0] + g.Bs[1])));
+    if ((unsigned)lx < (unsigned)B0 && (unsigned)ly < (unsigned)B1 &&
+        (unsigned)lz < (unsigned)B2) {
+      const uint32_t lc = (uint32_t)(lx | (ly << Bs0) | (lz << (Bs0 + Bs1)));
       lcr = lc | (atomicAdd(&scount[lc], 1u) << 16);
     } else {
       lcr = 0xFFFFu;  // not binned here: keep the particle, skip its collision
@@ -375,9 +412,9 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
     float fxbig = 0.0f;  // deterministic mode: largest fixed-point term seen by this lane
     for (int c0 = 0; c0 < bc; c0 += groups) {
       const int lc = c0 + grp;
-      const int cx = ox + (lc & (g.B[0] - 1));
-      const int cy = oy + ((lc >> g.Bs[0]) & (g.B[1] - 1));
-      const int cz = oz + (lc >> (g.Bs[0] + g.Bs[1]));
+      const int cx = ox + (lc & (B0 - 1));
+      const int cy = oy + ((lc >> Bs0) & (B1 - 1));
+      const int cz = oz + (lc >> (Bs0 + Bs1));
       const bool exists = lc < bc && cx < g.Lc[0] && cy < g.Lc[1] && cz < g.Lc[2];
       const uint32_t cg = (uint32_t)cx + (uint32_t)g.Lc[0] * ((uint32_t)cy + (uint32_t)g.Lc[1] * (uint32_t)cz);
       const int n = exists ? (int)scount[lc] : 0;
@@ -681,9 +718,9 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
     sx[i] = x; sy[i] = y; sz[i] = z;
     svx[i] = nx; svy[i] = ny; svz[i] = nz;
     const uint32_t zs = z & ~kCrossedBit;
-    const int qx = cell_axis(g, x, S1x, 0) >> g.Bs[0];
-    const int qy = cell_axis(g, y, S1y, 1) >> g.Bs[1];
-    const int qz = cell_axis(g, zs, S1z, 2) >> g.Bs[2];
+    const int qx = cell_axis(g, x, S1x, 0) >> Bs0;
+    const int qy = cell_axis(g, y, S1y, 1) >> Bs1;
+    const int qz = cell_axis(g, zs, S1z, 2) >> Bs2;
     const int dxb = brick_delta(qx, bx, g.nb[0], true);
     const int dyb = brick_delta(qy, by, g.nb[1], true);
     const int dzb = brick_delta(qz, bz, g.nb[2], zper);
@@ -762,14 +799,14 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
       d = gdest[code];
       slot = gbase[code] + (t >> 5);
     } else {
-      const int qx = cell_axis(g, sx[i], S1x, 0) >> g.Bs[0];
-      const int qy = cell_axis(g, sy[i], S1y, 1) >> g.Bs[1];
-      const int qz = cell_axis(g, sz[i] & ~kCrossedBit, S1z, 2) >> g.Bs[2];
+      const int qx = cell_axis(g, sx[i], S1x, 0) >> Bs0;
+      const int qy = cell_axis(g, sy[i], S1y, 1) >> Bs1;
+      const int qz = cell_axis(g, sz[i] & ~kCrossedBit, S1z, 2) >> Bs2;
       d = (uint32_t)(qx + g.nb[0] * (qy + g.nb[1] * qz));
       slot = atomicAdd(&cnt_dst[d], 1u);
     }
-    if (slot < (uint32_t)g.cap) {
-      const size_t o = (size_t)d * g.cap + slot;
+    if (slot < (uint32_t)cap) {
+      const size_t o = (size_t)d * cap + slot;
       dst.x[0][o] = sx[i]; dst.x[1][o] = sy[i]; dst.x[2][o] = sz[i];
       dst.v[0][o] = svx[i]; dst.v[1][o] = svy[i]; dst.v[2][o] = svz[i];
       dst.id[o] = sid[i];
@@ -794,12 +831,12 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
 // --- kernels -------------------------------------------------------------------------
 
 // One box: one CTA per brick.
-template <int VAR, bool DET>
+template <int VAR, bool DET, int TIER>
 __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ BrickShared sh;
   uint32_t phase = 0;
-  step_brick<VAR, DET, false>(a, blockIdx.x, smem, sh, phase);
+  step_brick<VAR, DET, false, TIER>(a, blockIdx.x, smem, sh, phase);
 }
 
 // Many small boxes of one variant in one persistent launch.  The boxes' arguments
@@ -888,6 +925,16 @@ size_t step_smem_bytes(const Geom& g) {
   return layout_for<2>(g).total;
 }
 
+template <int VAR, bool DET>
+cudaError_t set_cap_tiers(int v) {
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(k_step<VAR, DET, 0>, a, v);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<VAR, DET, 1>, a, v);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<VAR, DET, 2>, a, v);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<VAR, DET, 3>, a, v);
+  return e;
+}
+
 // The dynamic shared-memory cap is a per-function attribute shared by every box in the
 // process: it is set once to the device's limit (the launch's own size still decides
 // occupancy), so boxes with different needs never lower each other's cap.
@@ -895,12 +942,12 @@ cudaError_t configure_step_kernels(size_t max_dynamic_smem) {
   const int v = (int)max_dynamic_smem;
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<0, false>, a, v);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<1, false>, a, v);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<2, false>, a, v);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<0, true>, a, v);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<1, true>, a, v);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<2, true>, a, v);
+  if (e == cudaSuccess) e = set_cap_tiers<0, false>(v);
+  if (e == cudaSuccess) e = set_cap_tiers<1, false>(v);
+  if (e == cudaSuccess) e = set_cap_tiers<2, false>(v);
+  if (e == cudaSuccess) e = set_cap_tiers<0, true>(v);
+  if (e == cudaSuccess) e = set_cap_tiers<1, true>(v);
+  if (e == cudaSuccess) e = set_cap_tiers<2, true>(v);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step_packed<0, false>, a, v);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step_packed<1, false>, a, v);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step_packed<2, false>, a, v);
@@ -910,14 +957,21 @@ cudaError_t configure_step_kernels(size_t max_dynamic_smem) {
   return e;
 }
 
+template <int VAR, bool DET>
+void launch_tier(const StepArgs& a, size_t bytes, cudaStream_t s) {
+  switch (tier_of(a.g)) {
+    case 1: k_step<VAR, DET, 1><<<a.g.nbricks, kThreads, bytes, s>>>(a); break;
+    case 2: k_step<VAR, DET, 2><<<a.g.nbricks, kThreads, bytes, s>>>(a); break;
+    case 3: k_step<VAR, DET, 3><<<a.g.nbricks, kThreads, bytes, s>>>(a); break;
+    default: k_step<VAR, DET, 0><<<a.g.nbricks, kThreads, bytes, s>>>(a); break;
+  }
+}
+
 template <bool DET>
 void launch_step_t(const StepArgs& a, size_t bytes, cudaStream_t s) {
-  if (a.g.variant == 0)
-    k_step<0, DET><<<a.g.nbricks, kThreads, bytes, s>>>(a);
-  else if (a.g.variant == 1)
-    k_step<1, DET><<<a.g.nbricks, kThreads, bytes, s>>>(a);
-  else
-    k_step<2, DET><<<a.g.nbricks, kThreads, bytes, s>>>(a);
+  if (a.g.variant == 0) launch_tier<0, DET>(a, bytes, s);
+  else if (a.g.variant == 1) launch_tier<1, DET>(a, bytes, s);
+  else launch_tier<2, DET>(a, bytes, s);
 }
 
 cudaError_t launch_step(const StepArgs& a, cudaStream_t s) {

@@ -1,13 +1,16 @@
 """Shear viscosity of the GPU fluid from the decay of a transverse shear wave.
 
 A velocity profile v_x = A sin(k z) (k = 2 pi / L) decays as exp(-nu k^2 t) with the
-kinematic viscosity nu = eta / rho (rho = N_c m); the estimate is averaged over four
-independent boxes.  Checked, within 2 %, against:
-  * SRD (N_c 10, h 0.1, alpha 130 deg): the kinetic + collisional closed form of the
-    transport theory the paper cites, eta = 8.700 (0.486 + 8.214), and the oracle's own
-    estimate from a Poiseuille profile between no-slip walls;
-  * MPC-SRD+a (N_c 50, h 0.02, alpha 130 deg): the value the paper prints for this
-    parameter set in its squirmer showcase (Sec. V.B), eta = 111.3 sqrt(m kT)/a^2.
+kinematic viscosity nu = eta / rho (rho = N_c m); the estimate is averaged over
+independent boxes.  Checked against:
+  * SRD (N_c 10, h 0.1, alpha 130 deg): within 2 % of the kinetic + collisional closed
+    form of the transport theory the paper cites, eta = 8.700 (0.486 + 8.214), and of the
+    oracle's own estimate from a Poiseuille profile between no-slip walls;
+  * MPC-SRD+a (N_c 50, h 0.02, alpha 130 deg): within 2 % of the oracle's shear-wave
+    estimate, and within 3 % of the value the paper prints for this parameter set in its
+    squirmer showcase (Sec. V.B), eta = 111.3 sqrt(m kT)/a^2 (both implementations
+    measure ~109);
+plus Green-Kubo estimates of served and batched boxes against the SRD closed forms.
 """
 import numpy as np
 import pytest
@@ -69,10 +72,54 @@ def test_srd_viscosity_matches_closed_form_and_oracle():
     assert abs(eta - eta_oracle) / eta_oracle < 0.02
 
 
-def test_srd_a_viscosity_matches_printed_value():
+def _oracle_shear_eta(args):
+    """The same shear-wave estimate on the oracle (runs in a spawned process)."""
+    import oracle
+
+    variant, n_c, h, L, steps, samples, A, seed = args
+    p = oracle.params(L=L, n_c=n_c, h=h, alpha_deg=130.0, variant=variant, seed=seed)
+    X, V, ids = oracle.init(p)
+    F = oracle.fixed_bits(p)
+    for s in range(20):
+        r = oracle.step(p, X, V, ids, s)
+        X, V = r["X"], r["V"]
+    k = 2 * np.pi / L
+    V = V.copy()
+    V[0] += (A * np.sin(k * X[2] / 2.0**F)).astype(np.float32).astype(np.float64)
+    t, amp, s = [], [], 20
+    for j in range(samples + 1):
+        amp.append(2.0 * np.mean(V[0] * np.sin(k * X[2] / 2.0**F)))
+        t.append((s - 20) * h)
+        if j < samples:
+            for _ in range(steps // samples):
+                r = oracle.step(p, X, V, ids, s)
+                X, V = r["X"], r["V"]
+                s += 1
+    return -np.polyfit(np.array(t), np.log(np.array(amp)), 1)[0] / k**2 * n_c
+
+
+def test_srd_a_viscosity_matches_oracle_and_printed_value():
+    """MPC-SRD+a, N_c 50, h 0.02: the GPU shear-wave viscosity agrees with the oracle's
+    (same estimator, L = 16, independent seeds) within 2 %, and with the value the paper
+    prints (111.3, the mean-field closed form) within 3 % at L = 48 -- both
+    implementations measure ~109, 2 % below the closed form, a gap of the closed form at
+    this density and time step, not of the kernel."""
+    import multiprocessing as mp
+    import os
+
+    import oracle
+
+    oracle.build()
+    jobs = [(2, 50.0, 0.02, 16, 300, 20, 0.3, seed) for seed in range(1, 17)]
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        ref = np.array(pool.map(_oracle_shear_eta, jobs))
+    gpu16 = np.array([shear_wave_eta(2, 50.0, 0.02, 16, 300, 20, seed=100 + s) for s in range(32)])
     eta, err = _mean_eta(2, 50.0, 0.02, L=48, steps=2600)
-    print(f"SRD+a shear-wave eta = {eta:.2f} +- {err:.2f}; paper 111.3")
-    assert abs(eta - 111.3) / 111.3 < 0.02
+    print(f"SRD+a: oracle L=16 {ref.mean():.2f} +- {ref.std(ddof=1) / 4:.2f}; GPU L=16 "
+          f"{gpu16.mean():.2f} +- {gpu16.std(ddof=1) / np.sqrt(32):.2f}; GPU L=48 {eta:.2f} +- "
+          f"{err:.2f}; paper 111.3")
+    assert abs(gpu16.mean() - ref.mean()) / ref.mean() < 0.02
+    assert abs(eta - 111.3) / 111.3 < 0.03
 
 
 def test_green_kubo_viscosity_of_served_boxes():
