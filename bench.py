@@ -397,7 +397,8 @@ def run_serving(args, mpc) -> dict:
     job trace run one job at a time on the plain path, at the stated arrival rate (more
     work than the GPU can do: latency grows with the queue) and at 70 % of the served
     throughput measured on the first trace.  At the stated rate the served form is also
-    run with every resident job stepping in every chunk."""
+    run with every resident job stepping in every chunk, at 70 % with the stepping jobs
+    picked in arrival order (first come) instead of by least remaining work."""
     budget = 150 * 10**9
     out = {"workload": "viscosity jobs: L uniform in {16..96}, N_c=10, SRD 90/130 deg or AT+a, "
                        "h in {0.02,0.05,0.1}, steps log-uniform 1k-20k, Poisson arrivals; "
@@ -418,8 +419,10 @@ def run_serving(args, mpc) -> dict:
     light = serving_trace(args.serve_jobs, rate, seed=6)
     served = serve_once(mpc, light, budget, False)
     plain = serve_once(mpc, light, budget, True)
+    fifo = serve_once(mpc, light, budget, False, first_come=True)
     out[f"rate_70pct_of_capacity"] = {"arrival_rate_per_s": rate, "served": served,
                                       "sequential_plain": plain,
+                                      "served_first_come": fifo,
                                       "p99_ratio_plain_over_served":
                                           plain["p99_latency_s"] / served["p99_latency_s"],
                                       "p50_ratio_plain_over_served":
