@@ -56,6 +56,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-observables", action="store_true",
                     help="do not accumulate observables inside the step (they are then "
                          "reduced from the state when read)")
+    ap.add_argument("--no-det", action="store_true",
+                    help="skip timing the deterministic (fixed-point) mode")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-ensemble leg")
     ap.add_argument("--batch-boxes", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=100)
@@ -259,6 +261,28 @@ def run_reference(args):
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+# --- deterministic mode ------------------------------------------------------------------------------
+
+def run_deterministic(args, mpc, torch, kw, float_ms: float) -> dict:
+    """The same workload with fixed-point cell sums and observables (bit-reproducible
+    trajectories, Sec. III.B "Reproducibility"): its step time against the float mode."""
+    sim = mpc.Simulation(**dict(kw, flags=kw["flags"] | mpc.MPC_FLAG_DETERMINISTIC))
+    stream = torch.cuda.current_stream()
+    sim.step(args.warmup)
+    sim.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    sim.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    n = sim.N
+    sim.close()
+    return {"ms_per_step": ms, "particle_steps_per_s": n / (ms / 1e3),
+            "slowdown_vs_float": ms / float_ms}
 
 
 # --- batched ensemble --------------------------------------------------------------------------------
@@ -533,6 +557,10 @@ def run_ours(args):
 
     sim.close()
     torch.cuda.empty_cache()  # the box's memory came from torch's caching allocator
+    deterministic = None
+    if rank == 0 and world == 1 and not args.no_det:
+        deterministic = run_deterministic(args, mpc, torch, kw, ms_max / args.steps)
+        torch.cuda.empty_cache()
     batched = None
     if rank == 0 and world == 1 and not args.no_batch:
         batched = run_batched(args, mpc, torch)
@@ -554,7 +582,7 @@ def run_ours(args):
                 "clocks": clk,
                 "checks": {"momentum": [float(x) for x in obs["momentum"]],
                            "temperature": obs["temperature"], "step": obs["step"]},
-                "batched": batched, "serving": serving}
+                "deterministic": deterministic, "batched": batched, "serving": serving}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

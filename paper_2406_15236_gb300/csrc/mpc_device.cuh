@@ -60,6 +60,11 @@ __device__ __forceinline__ float2 normal2(uint32_t ra, uint32_t rb) {
   return make_float2(R * c, R * s);
 }
 
+// the first (cosine) normal of the Box-Muller pair alone
+__device__ __forceinline__ float normal_cos(uint32_t ra, uint32_t rb) {
+  return sqrtf(-2.0f * logf(u01(ra))) * cospif(2.0f * u01(rb));
+}
+
 // Gamma(shape a >= 1, scale 1), Marsaglia & Tsang (ACM TOMS 26, 2000); attempt k uses
 // Philox(index, step, tag, k).  Float32 decisions in a fixed evaluation order.
 __device__ __forceinline__ float gamma_mt(const Geom& g, uint32_t index, uint32_t step, uint32_t tag,

@@ -166,6 +166,39 @@ __device__ __forceinline__ float group_sum(float v, int tpc) {
   return v;
 }
 
+// Warp sums of 16 values at once: at each butterfly level a lane keeps half of its
+// values and adds the partner's copy of that half (the other half goes to the partner),
+// so 16 + 8 + 4 + 2 + 1 exchanges replace 16 x 5.  Lanes 2j and 2j + 1 end with the sum
+// of value j over the warp.
+template <class T>
+__device__ __forceinline__ T warp_reduce_scatter16(T (&v)[16], int lane) {
+  const bool hi8 = lane & 16, hi4 = lane & 8, hi2 = lane & 4, hi1 = lane & 2;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const T send = hi8 ? v[k] : v[k + 8];
+    const T keep = hi8 ? v[k + 8] : v[k];
+    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const T send = hi4 ? v[k] : v[k + 4];
+    const T keep = hi4 ? v[k + 4] : v[k];
+    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const T send = hi2 ? v[k] : v[k + 2];
+    const T keep = hi2 ? v[k + 2] : v[k];
+    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  {
+    const T send = hi1 ? v[0] : v[1];
+    const T keep = hi1 ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
 // brick-axis offset of a neighbour: 0 same, +-1 adjacent (with periodic wrap), 9 other
 __device__ __forceinline__ int brick_delta(int q, int b, int nb, bool periodic) {
   int d = q - b;
@@ -365,7 +398,7 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
       // AT+a: keep v_ran and w = v - v_ran
       const uint4 r = draw(g, sid[i], step, kTagAtVel, 0u);
       const float2 n01 = normal2(r.x, r.y);
-      const float n2 = normal2(r.z, r.w).x;
+      const float n2 = normal_cos(r.z, r.w);
       const float ux = g.sigma * n01.x, uy = g.sigma * n01.y, uz = g.sigma * n2;
       sux[i] = ux; suy[i] = uy; suz[i] = uz;
       vx -= ux; vy -= uy; vz -= uz;
@@ -747,18 +780,15 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
   if (g.obs) {
     const int w = tid >> 5;
     if constexpr (DET) {
-#pragma unroll
-      for (int q = 0; q < 13; ++q) {
-        const long long s = warp_sum_fx(o_q[q]);
-        if (lane == 0) sh.obs.q[w][q] = s;
-      }
+      long long vals[16] = {o_q[0], o_q[1], o_q[2], o_q[3], o_q[4], o_q[5], o_q[6], o_q[7],
+                            o_q[8], o_q[9], o_q[10], o_q[11], o_q[12], 0, 0, 0};
+      const long long s = warp_reduce_scatter16(vals, lane);
+      if (!(lane & 1) && (lane >> 1) < 13) sh.obs.q[w][lane >> 1] = s;
     } else {
-      float vals[13] = {o_px, o_py, o_pz, o_e, o_kxy, o_kyz, o_kzx, o_c[0], o_c[1], o_c[2], o_c[3], o_c[4], o_c[5]};
-#pragma unroll
-      for (int q = 0; q < 13; ++q) {
-        const float s = warp_sum(vals[q]);
-        if (lane == 0) sh.obs.f[w][q] = s;
-      }
+      float vals[16] = {o_px, o_py, o_pz, o_e, o_kxy, o_kyz, o_kzx, o_c[0], o_c[1], o_c[2],
+                        o_c[3], o_c[4], o_c[5], 0.f, 0.f, 0.f};
+      const float s = warp_reduce_scatter16(vals, lane);
+      if (!(lane & 1) && (lane >> 1) < 13) sh.obs.f[w][lane >> 1] = s;
     }
   }
   __syncthreads();
