@@ -3,8 +3,9 @@
 // One batch step advances every member by one MPC step:
 //   - members large enough to fill the GPU alone (at least two waves of bricks) get
 //     their own launch of the single-box kernel;
-//   - the other members are packed, grouped by variant (kPackGroup boxes at most per
-//     group), and each group is one persistent launch of the packed kernel, which
+//   - the other members are packed, grouped by variant and brick geometry (kPackGroup
+//     boxes at most per group), and each group is one persistent launch of the packed
+//     kernel (with the geometry compiled in when it is a default one), which
 //     carries the boxes' arguments in kernel parameter space and lets its CTAs claim
 //     the group's bricks from a counter;
 //   - one small launch closes the step of every member (step counter, observables).
@@ -218,6 +219,7 @@ struct mpc_batch_s {
   uint32_t* counters = nullptr;     // one work-claiming counter per packed group
   struct Group {
     int variant = 0;
+    int tier = 0;  // brick geometry compiled into the launch (0: any)
     size_t smem = 0;
     int grid = 0, ctas_per_sm = 0;
     PackTable table{};
@@ -307,16 +309,20 @@ mpc_status refresh(mpc_batch b) {
   }
   std::stable_sort(packed.begin(), packed.end(), [](mpc_handle x, mpc_handle y) {
     if (x->g.variant != y->g.variant) return x->g.variant < y->g.variant;
+    const int tx = brick_tier(x->g), ty = brick_tier(y->g);
+    if (tx != ty) return tx > ty;
     return step_smem_bytes(x->g) < step_smem_bytes(y->g);
   });
   b->groups.clear();
   int64_t items = 0;
   for (size_t i = 0; i < packed.size(); ++i) {
     mpc_handle h = packed[i];
+    const int tier = brick_tier(h->g);
     if (b->groups.empty() || b->groups.back().variant != h->g.variant ||
-        b->groups.back().table.n == kPackGroup) {
+        b->groups.back().tier != tier || b->groups.back().table.n == kPackGroup) {
       b->groups.emplace_back();
       b->groups.back().variant = h->g.variant;
+      b->groups.back().tier = tier;
     }
     mpc_batch_s::Group& G = b->groups.back();
     PackTable& P = G.table;
@@ -332,7 +338,7 @@ mpc_status refresh(mpc_batch b) {
   for (size_t gi = 0; gi < b->groups.size(); ++gi) {
     mpc_batch_s::Group& G = b->groups[gi];
     G.table.counter = b->counters + gi;
-    BCU(b, packed_kernel_occupancy(G.variant, b->det, G.smem, &G.ctas_per_sm));
+    BCU(b, packed_kernel_occupancy(G.variant, G.tier, b->det, G.smem, &G.ctas_per_sm));
     if (G.ctas_per_sm < 1) return bfail(b, MPC_EINVAL, "the packed step kernel does not fit on an SM");
     G.grid = (int)std::min<int64_t>(G.table.begin[G.table.n], (int64_t)G.ctas_per_sm * b->num_sms);
   }
@@ -362,7 +368,7 @@ cudaError_t launch_batch_step(mpc_batch b, cudaStream_t s) {
     e = launch_step(b->solo_args[i], on(i));
   for (size_t i = 0; i < b->groups.size() && e == cudaSuccess; ++i) {
     const mpc_batch_s::Group& G = b->groups[i];
-    e = launch_step_packed(G.table, G.variant, b->det, G.grid, G.smem, on(b->solo_args.size() + i));
+    e = launch_step_packed(G.table, G.variant, G.tier, b->det, G.grid, G.smem, on(b->solo_args.size() + i));
   }
   if (e == cudaSuccess && nb > 1) {
     for (int k = 0; k < nb && e == cudaSuccess; ++k) {

@@ -113,9 +113,11 @@ cudaError_t configure_step_kernels(size_t max_dynamic_smem);
 cudaError_t launch_step(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_advance(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_store_i64(int64_t* p, int64_t v, cudaStream_t s);
-// packed step of many small boxes of one variant: CTAs of the kernel per SM, launch
-cudaError_t packed_kernel_occupancy(int variant, bool det, size_t smem_bytes, int* ctas_per_sm);
-cudaError_t launch_step_packed(const PackTable& t, int variant, bool det, int grid,
+// packed step of many small boxes of one variant and brick tier (all boxes of a launch
+// share the tier; tier 0 = any geometry): CTAs of the kernel per SM, launch
+int brick_tier(const Geom& g);
+cudaError_t packed_kernel_occupancy(int variant, int tier, bool det, size_t smem_bytes, int* ctas_per_sm);
+cudaError_t launch_step_packed(const PackTable& t, int variant, int tier, bool det, int grid,
                                size_t smem_bytes, cudaStream_t s);
 // closes the step of every member of a batch
 cudaError_t launch_advance_batch(const BatchTable* t, int grid, cudaStream_t s);

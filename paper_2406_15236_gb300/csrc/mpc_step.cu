@@ -875,7 +875,7 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
 // kernel rather than per-thread registers.  CTAs claim work items (bricks of the
 // packed boxes, box k owning items [begin[k], begin[k+1])) from a counter that is zero
 // at launch; each CTA's claims increase, so its box index only moves forward.
-template <int VAR, bool DET>
+template <int VAR, bool DET, int TIER>
 __global__ void __launch_bounds__(kThreads) k_step_packed(const __grid_constant__ PackTable p) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ BrickShared sh;
@@ -891,7 +891,7 @@ __global__ void __launch_bounds__(kThreads) k_step_packed(const __grid_constant_
     const int w = s_w;
     if (w >= total) return;
     while (k + 1 < p.n && p.begin[k + 1] <= w) ++k;
-    if (!step_brick<VAR, DET, true>(p.args[k], w - p.begin[k], smem, sh, phase)) return;
+    if (!step_brick<VAR, DET, true, TIER>(p.args[k], w - p.begin[k], smem, sh, phase)) return;
     // the next item's bulk copies overwrite shared memory this item wrote
     fence_proxy_async_smem();
     __syncthreads();
@@ -962,6 +962,10 @@ cudaError_t set_cap_tiers(int v) {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<VAR, DET, 1>, a, v);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<VAR, DET, 2>, a, v);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<VAR, DET, 3>, a, v);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step_packed<VAR, DET, 0>, a, v);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step_packed<VAR, DET, 1>, a, v);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step_packed<VAR, DET, 2>, a, v);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step_packed<VAR, DET, 3>, a, v);
   return e;
 }
 
@@ -978,12 +982,7 @@ cudaError_t configure_step_kernels(size_t max_dynamic_smem) {
   if (e == cudaSuccess) e = set_cap_tiers<0, true>(v);
   if (e == cudaSuccess) e = set_cap_tiers<1, true>(v);
   if (e == cudaSuccess) e = set_cap_tiers<2, true>(v);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step_packed<0, false>, a, v);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step_packed<1, false>, a, v);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step_packed<2, false>, a, v);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step_packed<0, true>, a, v);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step_packed<1, true>, a, v);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step_packed<2, true>, a, v);
+
   return e;
 }
 
@@ -1021,33 +1020,53 @@ cudaError_t launch_store_i64(int64_t* p, int64_t v, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <bool DET>
-cudaError_t packed_occupancy_t(int variant, size_t smem_bytes, int* ctas_per_sm) {
-  if (variant == 0)
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_step_packed<0, DET>, kThreads, smem_bytes);
-  if (variant == 1)
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_step_packed<1, DET>, kThreads, smem_bytes);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_step_packed<2, DET>, kThreads, smem_bytes);
-}
-
-cudaError_t packed_kernel_occupancy(int variant, bool det, size_t smem_bytes, int* ctas_per_sm) {
-  return det ? packed_occupancy_t<true>(variant, smem_bytes, ctas_per_sm)
-             : packed_occupancy_t<false>(variant, smem_bytes, ctas_per_sm);
+template <int VAR, bool DET>
+cudaError_t packed_occupancy_v(int tier, size_t smem_bytes, int* ctas_per_sm) {
+  switch (tier) {
+    case 1: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_step_packed<VAR, DET, 1>, kThreads, smem_bytes);
+    case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_step_packed<VAR, DET, 2>, kThreads, smem_bytes);
+    case 3: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_step_packed<VAR, DET, 3>, kThreads, smem_bytes);
+    default: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_step_packed<VAR, DET, 0>, kThreads, smem_bytes);
+  }
 }
 
 template <bool DET>
-void launch_packed_t(const PackTable& t, int variant, int grid, size_t smem_bytes, cudaStream_t s) {
-  if (variant == 0) k_step_packed<0, DET><<<grid, kThreads, smem_bytes, s>>>(t);
-  else if (variant == 1) k_step_packed<1, DET><<<grid, kThreads, smem_bytes, s>>>(t);
-  else k_step_packed<2, DET><<<grid, kThreads, smem_bytes, s>>>(t);
+cudaError_t packed_occupancy_t(int variant, int tier, size_t smem_bytes, int* ctas_per_sm) {
+  if (variant == 0) return packed_occupancy_v<0, DET>(tier, smem_bytes, ctas_per_sm);
+  if (variant == 1) return packed_occupancy_v<1, DET>(tier, smem_bytes, ctas_per_sm);
+  return packed_occupancy_v<2, DET>(tier, smem_bytes, ctas_per_sm);
 }
 
-cudaError_t launch_step_packed(const PackTable& t, int variant, bool det, int grid,
+cudaError_t packed_kernel_occupancy(int variant, int tier, bool det, size_t smem_bytes, int* ctas_per_sm) {
+  return det ? packed_occupancy_t<true>(variant, tier, smem_bytes, ctas_per_sm)
+             : packed_occupancy_t<false>(variant, tier, smem_bytes, ctas_per_sm);
+}
+
+template <int VAR, bool DET>
+void launch_packed_v(const PackTable& t, int tier, int grid, size_t smem_bytes, cudaStream_t s) {
+  switch (tier) {
+    case 1: k_step_packed<VAR, DET, 1><<<grid, kThreads, smem_bytes, s>>>(t); break;
+    case 2: k_step_packed<VAR, DET, 2><<<grid, kThreads, smem_bytes, s>>>(t); break;
+    case 3: k_step_packed<VAR, DET, 3><<<grid, kThreads, smem_bytes, s>>>(t); break;
+    default: k_step_packed<VAR, DET, 0><<<grid, kThreads, smem_bytes, s>>>(t); break;
+  }
+}
+
+template <bool DET>
+void launch_packed_t(const PackTable& t, int variant, int tier, int grid, size_t smem_bytes, cudaStream_t s) {
+  if (variant == 0) launch_packed_v<0, DET>(t, tier, grid, smem_bytes, s);
+  else if (variant == 1) launch_packed_v<1, DET>(t, tier, grid, smem_bytes, s);
+  else launch_packed_v<2, DET>(t, tier, grid, smem_bytes, s);
+}
+
+cudaError_t launch_step_packed(const PackTable& t, int variant, int tier, bool det, int grid,
                                size_t smem_bytes, cudaStream_t s) {
-  if (det) launch_packed_t<true>(t, variant, grid, smem_bytes, s);
-  else launch_packed_t<false>(t, variant, grid, smem_bytes, s);
+  if (det) launch_packed_t<true>(t, variant, tier, grid, smem_bytes, s);
+  else launch_packed_t<false>(t, variant, tier, grid, smem_bytes, s);
   return cudaGetLastError();
 }
+
+int brick_tier(const Geom& g) { return tier_of(g); }
 
 cudaError_t launch_advance_batch(const BatchTable* t, int grid, cudaStream_t s) {
   k_advance_batch<<<grid, kObsSlots, 0, s>>>(t);
