@@ -214,15 +214,30 @@ __device__ __forceinline__ int brick_delta(int q, int b, int nb, bool periodic) 
 // exactly, so a cell's sums do not depend on the order of its members, on the brick
 // geometry or on the number of cooperating threads.  Terms must stay below 2^15 in
 // magnitude (|t| n < 2^31 for the largest admissible cell); larger terms raise
-// kErrFixedRange.  A float32 term above 2^-9 converts without rounding.
+// kErrFixedRange.  A float32 term above 2^-9 converts without rounding (smaller terms are
+// truncated toward zero at 2^-32).
 constexpr float kFx = 4294967296.0f;               // 2^32
 constexpr float kUnFx = 2.3283064365386963e-10f;   // 2^-32
 constexpr float kFxLimit = 32768.0f;
 // observables: 24 fraction bits (sums over whole boxes of up to ~2^30 particles)
-constexpr float kObsFx = 16777216.0f;              // 2^24
 constexpr double kObsUnFx = 5.9604644775390625e-08; // 2^-24
 
-__device__ __forceinline__ long long to_fx(float v) { return __float2ll_rn(v * kFx); }
+// v * 2^S as a 64-bit integer, from the IEEE-754 fields with integer operations only (the
+// float-to-int64 conversion instruction issues at the FP64 rate on this GPU and made the
+// deterministic step twice as slow): exact when v * 2^S is an integer, else truncated
+// toward zero; |v| < 2^(38 - S) assumed (the callers' range checks flag larger terms).
+template <int S>
+__device__ __forceinline__ long long fixed_of(float v) {
+  const uint32_t b = __float_as_uint(v);
+  const int e = (int)((b >> 23) & 0xFFu);
+  const unsigned long long m = (b & 0x7FFFFFu) | (e != 0 ? 0x800000u : 0u);
+  const int sh = e - (127 + 23 - S);  // v * 2^S = m * 2^sh
+  const unsigned long long r = sh >= 0 ? (m << min(sh, 38)) : (m >> min(-sh, 32));
+  const long long q = (long long)r;
+  return (b >> 31) ? -q : q;
+}
+
+__device__ __forceinline__ long long to_fx(float v) { return fixed_of<32>(v); }
 __device__ __forceinline__ float from_fx(long long s) { return __ll2float_rn(s) * kUnFx; }
 
 __device__ __forceinline__ long long group_sum_fx(long long v, int tpc) {
@@ -735,7 +750,7 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
         const float t[13] = {nx, ny, nz, nx * nx + ny * ny + nz * nz, vbx * vby, vby * vbz,
                              vbz * vbx, dx * py, dy * px, dy * pz, dz * py, dz * px, dx * pz};
 #pragma unroll
-        for (int q = 0; q < 13; ++q) o_q[q] += __float2ll_rn(t[q] * kObsFx);
+        for (int q = 0; q < 13; ++q) o_q[q] += fixed_of<24>(t[q]);
       } else {
         o_px += nx; o_py += ny; o_pz += nz;
         o_e += nx * nx + ny * ny + nz * nz;
