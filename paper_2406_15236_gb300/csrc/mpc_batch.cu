@@ -565,7 +565,7 @@ mpc_status mpc_batch_create(const mpc_batch_config* cfg, void* stream, mpc_batch
   for (int k = 0; k < kTableBuffers; ++k) {
     if (cudaMallocHost(&b->table_host[k], sizeof(BatchTable)) != cudaSuccess) {
       b->table_host[k] = nullptr;
-      return bail(MPC_ENOMEM, "pinned host allocation failed: work table");
+      return bail(MPC_ENOMEM, "pinned host allocation failed: member table");
     }
     if (cudaEventCreateWithFlags(&b->table_ev[k], cudaEventDisableTiming) != cudaSuccess)
       return bail(MPC_ECUDA, "event creation failed");
