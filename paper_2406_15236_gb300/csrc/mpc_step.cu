@@ -4,8 +4,9 @@
 // will occupy in the coming step, with their positions already streamed for that step
 // (Eq. 1 with gravity kick and periodic / bounce-back walls; a wall crossing is kept in
 // bit 31 of z) and the velocity they streamed with.  For step n a CTA
-//   1. pulls its brick's particles (x, y, z, vx, vy, vz, id: 28 B each) into shared
-//      memory with bulk-async (TMA) copies,
+//   1. pulls its brick's particles (x, y, z, vx, vy, vz: 24 B each; the 4-byte ids too
+//      for AT+a, whose random velocities are keyed by them) into shared memory with
+//      bulk-async (TMA) copies,
 //   2. finds their cell on the lattice shifted by S(n) -- inside this brick by
 //      construction -- and counting-sorts them by cell in shared memory (integer
 //      atomics give each particle its rank in its cell; a scan gives offsets),
@@ -16,11 +17,15 @@
 //   4. applies the collision to every particle, streams it for step n+1 (its only
 //      streaming per step), finds the brick of its next collision cell, ranks it within
 //      its destination group (warp-aggregated shared atomics), reserves space in each
-//      destination with one global atomic per (CTA, destination), and writes the
-//      particles out in contiguous runs.
-// HBM traffic per particle-step is one read and one write of the 28-byte particle:
-// no global per-cell arrays, no second sweep, no separate reorder pass (the permanent
-// reorder of Sec. III.B.3 happens in every step as part of the write).
+//      destination with one global atomic per (CTA, destination) while the ids are
+//      copied into the shared memory the cell lists used, and writes the particles out
+//      in contiguous runs.
+// HBM traffic per particle-step is one read and one write of the 28-byte particle (AT+a
+// reads its ids a second time, from L2): no global per-cell arrays, no second sweep, no
+// separate reorder pass (the permanent reorder of Sec. III.B.3 happens in every step as
+// part of the write).  Keeping the ids out of shared memory between the draws and the
+// write-out, 16-bit tags and the observables partials in the cell-list area bring a
+// brick to 27.9 KB (SRD) and 37.8 KB (AT+a): 8 and 6 CTAs per SM.
 #include <cstdio>
 
 #include "mpc_device.cuh"
@@ -48,13 +53,26 @@ struct CellParams<2> {  // SRD+a: v_cm (3), omega (3), rho_cm (3), rotation axis
   static constexpr bool kStoresRandomVelocity = false;
 };
 
+// Dynamic shared memory of one brick.  Two regions are reused over the phases of a
+// step: `cells` (member counts and list offsets, then the CTA's observables partials)
+// and `stage` (the particle ids for the random-velocity draws, then the member lists and
+// cell parameters, then the ids again for the write-out).
 struct Layout {
-  size_t x, y, z, vx, vy, vz, id, gcell, ux, uy, uz, tag, perm, count, cstart, params, total;
+  size_t x, y, z, vx, vy, vz, gcell, ux, uy, uz, tag, count, cstart, perm, params, total;
+};
+
+// per-warp partial sums of the 13 observables (aliases the `cells` region)
+union ObsShared {
+  float f[kThreads / 32][13];
+  long long q[kThreads / 32][13];
 };
 
 __host__ __device__ constexpr size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
-__host__ __device__ constexpr Layout make_layout(int cap, int bc, int nparams, bool vran, int debug) {
+__host__ __device__ constexpr size_t max_sz(size_t a, size_t b) { return a > b ? a : b; }
+
+__host__ __device__ constexpr Layout make_layout(int cap, int bc, int nparams, bool vran, int debug,
+                                                 int tag_bytes) {
   Layout L{};
   size_t o = 0;
   const size_t a4 = align16(size_t(cap) * 4);
@@ -64,25 +82,25 @@ __host__ __device__ constexpr Layout make_layout(int cap, int bc, int nparams, b
   L.vx = o; o += a4;
   L.vy = o; o += a4;
   L.vz = o; o += a4;
-  L.id = o; o += a4;
   L.gcell = o; o += debug ? a4 : 0;
   L.ux = o; o += vran ? a4 : 0;
   L.uy = o; o += vran ? a4 : 0;
   L.uz = o; o += vran ? a4 : 0;
-  L.tag = o; o += a4;
-  L.perm = o; o += align16(size_t(cap) * 2);
-  L.count = o; o += align16(size_t(bc) * 4);
-  L.cstart = o; o += align16(size_t(bc + 1) * 4);
-  L.params = o; o += align16(size_t(bc) * 4 * nparams);
+  L.tag = o; o += align16(size_t(cap) * tag_bytes);
+  // cells: counts and offsets, later the observables partials
+  const size_t cells = align16(size_t(bc) * 4) + align16(size_t(bc + 1) * 4);
+  L.count = o;
+  L.cstart = o + align16(size_t(bc) * 4);
+  o += max_sz(cells, align16(sizeof(ObsShared)));
+  // stage: ids, then member lists and cell parameters, then ids again
+  const size_t lists = align16(size_t(cap) * 2) + align16(size_t(bc) * 4 * nparams);
+  L.perm = o;
+  L.params = o + align16(size_t(cap) * 2);
+  o += max_sz(lists, a4);
   L.total = o;
   return L;
 }
 
-template <int VAR>
-__host__ __device__ inline Layout layout_for(const Geom& g) {
-  return make_layout(g.cap, g.brick_cells, CellParams<VAR>::kParams,
-                     CellParams<VAR>::kStoresRandomVelocity, g.debug);
-}
 
 // Brick geometries compiled in: the default ~640-particle tiles (capacity 864) of
 // 4x4x2, 4x4x4 and 8x4x4 cells.  With the shared-memory layout and the brick shape as
@@ -114,6 +132,34 @@ __host__ __device__ inline int tier_of(const Geom& g) {
   return 0;
 }
 
+// Per-particle tag: collision cell in the brick | rank in that cell (phases 2-4), then
+// destination code | rank in the destination group << 5 (phases 4-6).  Bricks of at
+// most 64 cells and 864 slots fit both in 16 bits (cell: low log2(cells) bits, rank
+// below 864); the others use 32 bits with the cell in the low 16.
+template <int TIER>
+struct TagOf {
+  using type = uint32_t;
+  static constexpr int kCellBits = 16;
+};
+template <>
+struct TagOf<1> {
+  using type = uint16_t;
+  static constexpr int kCellBits = 5;
+};
+template <>
+struct TagOf<2> {
+  using type = uint16_t;
+  static constexpr int kCellBits = 6;
+};
+constexpr uint32_t kNoCell = 0xFFFFu;  // tag of a particle not binned in this brick
+
+template <int VAR>
+__host__ __device__ inline Layout layout_for(const Geom& g) {
+  const int t = tier_of(g);
+  return make_layout(g.cap, g.brick_cells, CellParams<VAR>::kParams,
+                     CellParams<VAR>::kStoresRandomVelocity, g.debug, (t == 1 || t == 2) ? 2 : 4);
+}
+
 // --- small PTX wrappers -----------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -137,6 +183,10 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
           smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
+}
+
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
 // bounded wait on phase `parity`; false on timeout
@@ -216,7 +266,6 @@ __device__ __forceinline__ int brick_delta(int q, int b, int nb, bool periodic) 
 // magnitude (|t| n < 2^31 for the largest admissible cell); larger terms raise
 // kErrFixedRange.  A float32 term above 2^-9 converts without rounding (smaller terms are
 // truncated toward zero at 2^-32).
-constexpr float kFx = 4294967296.0f;               // 2^32
 constexpr float kUnFx = 2.3283064365386963e-10f;   // 2^-32
 constexpr float kFxLimit = 32768.0f;
 // observables: 24 fraction bits (sums over whole boxes of up to ~2^30 particles)
@@ -266,10 +315,6 @@ struct BrickShared {
   uint32_t cnt, halt;
   int64_t step;
   uint32_t gcount[28], gbase[28], gdest[28];
-  union {
-    float f[kThreads / 32][13];
-    long long q[kThreads / 32][13];
-  } obs;
 };
 
 // --- one brick of one box ---------------------------------------------------------
@@ -286,8 +331,11 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
   const int cap = TIER ? T::cap : g.cap;
   const int Bs0 = TIER ? T::Bs0 : g.Bs[0], Bs1 = TIER ? T::Bs1 : g.Bs[1], Bs2 = TIER ? T::Bs2 : g.Bs[2];
   const int B0 = 1 << Bs0, B1 = 1 << Bs1, B2 = 1 << Bs2;
+  using Tag = typename TagOf<TIER>::type;
+  constexpr int kCellBits = TagOf<TIER>::kCellBits;
+  constexpr uint32_t kCellMask = (1u << kCellBits) - 1u;
   const Layout lay = TIER ? make_layout(T::cap, 1 << (T::Bs0 + T::Bs1 + T::Bs2), CellParams<VAR>::kParams,
-                                        CellParams<VAR>::kStoresRandomVelocity, 0)
+                                        CellParams<VAR>::kStoresRandomVelocity, 0, (int)sizeof(Tag))
                           : layout_for<VAR>(g);
 
   uint32_t* sx = reinterpret_cast<uint32_t*>(smem + lay.x);
@@ -296,18 +344,17 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
   float* svx = reinterpret_cast<float*>(smem + lay.vx);  // SRD: v; AT+a: w = v - v_ran
   float* svy = reinterpret_cast<float*>(smem + lay.vy);
   float* svz = reinterpret_cast<float*>(smem + lay.vz);
-  uint32_t* sid = reinterpret_cast<uint32_t*>(smem + lay.id);
+  uint32_t* sid = reinterpret_cast<uint32_t*>(smem + lay.perm);  // stage: ids (phases 1-2, 5-6)
   uint32_t* sgc = reinterpret_cast<uint32_t*>(smem + lay.gcell);
   float* sux = reinterpret_cast<float*>(smem + lay.ux);  // AT+a: v_ran
   float* suy = reinterpret_cast<float*>(smem + lay.uy);
   float* suz = reinterpret_cast<float*>(smem + lay.uz);
-  // per particle: local cell | rank in cell << 16 (phases 2-4), then destination code |
-  // rank in destination group << 5 (phases 4-6)
-  uint32_t* stag = reinterpret_cast<uint32_t*>(smem + lay.tag);
-  uint16_t* sperm = reinterpret_cast<uint16_t*>(smem + lay.perm);
+  Tag* stag = reinterpret_cast<Tag*>(smem + lay.tag);
+  uint16_t* sperm = reinterpret_cast<uint16_t*>(smem + lay.perm);  // stage: member lists
   uint32_t* scount = reinterpret_cast<uint32_t*>(smem + lay.count);
   uint32_t* scstart = reinterpret_cast<uint32_t*>(smem + lay.cstart);
   float* spar = reinterpret_cast<float*>(smem + lay.params);
+  ObsShared& sobs = *reinterpret_cast<ObsShared*>(smem + lay.count);  // after the cells
 
   uint32_t* gcount = sh.gcount;
   uint32_t* gbase = sh.gbase;
@@ -335,7 +382,9 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
       a.cnt[p][b] = 0;  // this buffer becomes the destination of the next step
       if (!PERSIST) mbar_init(&sh.bar, 1);
       const uint32_t bytes = (uint32_t)(((c + 3) & ~3u) * 4);
-      mbar_expect_tx(&sh.bar, 7u * bytes);
+      // AT+a draws its random velocities from the ids now; the other variants need the
+      // ids only for the write-out, copied in again then (step 5)
+      mbar_expect_tx(&sh.bar, (VAR == 1 ? 7u : 6u) * bytes);
       if (bytes) {
         const PBuf& sb = a.buf[p];
         const size_t off = (size_t)b * cap;
@@ -345,7 +394,8 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
         bulk_g2s(svx, sb.v[0] + off, bytes, &sh.bar);
         bulk_g2s(svy, sb.v[1] + off, bytes, &sh.bar);
         bulk_g2s(svz, sb.v[2] + off, bytes, &sh.bar);
-        bulk_g2s(sid, sb.id + off, bytes, &sh.bar);
+        if (VAR == 1) bulk_g2s(sid, sb.id + off, bytes, &sh.bar);
+        else bulk_prefetch_l2(sb.id + off, bytes);
       }
     }
     sh.cnt = c;
@@ -402,12 +452,12 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
     if ((unsigned)lx < (unsigned)B0 && (unsigned)ly < (unsigned)B1 &&
         (unsigned)lz < (unsigned)B2) {
       const uint32_t lc = (uint32_t)(lx | (ly << Bs0) | (lz << (Bs0 + Bs1)));
-      lcr = lc | (atomicAdd(&scount[lc], 1u) << 16);
+      lcr = lc | (atomicAdd(&scount[lc], 1u) << kCellBits);
     } else {
-      lcr = 0xFFFFu;  // not binned here: keep the particle, skip its collision
+      lcr = kNoCell;  // not binned here: keep the particle, skip its collision
       atomicOr(&a.ctrl->errors, kErrBinning);
     }
-    stag[i] = lcr;
+    stag[i] = (Tag)lcr;
     if (g.debug) sgc[i] = (uint32_t)cx + (uint32_t)g.Lc[0] * ((uint32_t)cy + (uint32_t)g.Lc[1] * (uint32_t)cz);
     if constexpr (VAR == 1) {
       // AT+a: keep v_ran and w = v - v_ran
@@ -446,8 +496,7 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
   __syncthreads();
   for (int i = tid; i < cnt; i += kThreads) {
     const uint32_t lcr = stag[i];
-    const uint32_t lc = lcr & 0xFFFFu;
-    if (lc != 0xFFFFu) sperm[scstart[lc] + (lcr >> 16)] = (uint16_t)i;
+    if (lcr != kNoCell) sperm[scstart[lcr & kCellMask] + (lcr >> kCellBits)] = (uint16_t)i;
   }
   __syncthreads();
 
@@ -698,13 +747,14 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
   for (int i = tid; i < cnt; i += kThreads) {
     uint32_t x = sx[i], y = sy[i], z = sz[i] & ~kCrossedBit;
     float vbx = svx[i], vby = svy[i], vbz = svz[i];  // AT+a: w
-    const uint32_t lc = stag[i] & 0xFFFFu;
+    const uint32_t lcr = stag[i];
+    const uint32_t lc = lcr == kNoCell ? kNoCell : (lcr & kCellMask);
     float nx, ny, nz;
     // positions relative to the collision-cell centre (collisional stress, AT+a omega x r)
     const float px = rho_axis(g, x, S0x), py = rho_axis(g, y, S0y), pz = rho_axis(g, z, S0z);
     if constexpr (VAR == 0) {
       nx = vbx; ny = vby; nz = vbz;
-      if (lc != 0xFFFFu) {
+      if (lc != kNoCell) {
         const float* P = spar + lc;
         const float vcx = P[0], vcy = P[bc], vcz = P[2 * bc];
         const float ax = P[3 * bc], ay = P[4 * bc], az = P[5 * bc], kap = P[6 * bc];
@@ -718,7 +768,7 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
     } else if constexpr (VAR == 2) {
       // SRD+a, Eq. (3): v' = v_cm + D v_ic + omega x r_ic
       nx = vbx; ny = vby; nz = vbz;
-      if (lc != 0xFFFFu) {
+      if (lc != kNoCell) {
         const float* P = spar + lc;
         const float vcx = P[0], vcy = P[bc], vcz = P[2 * bc];
         const float wx = P[3 * bc], wy = P[4 * bc], wz = P[5 * bc];
@@ -735,7 +785,7 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
       const float ux = sux[i], uy = suy[i], uz = suz[i];
       vbx += ux; vby += uy; vbz += uz;  // the velocity the particle streamed with
       nx = vbx; ny = vby; nz = vbz;
-      if (lc != 0xFFFFu) {
+      if (lc != kNoCell) {
         const float* P = spar + lc;
         const float rx = px - P[6 * bc], ry = py - P[7 * bc], rz = pz - P[8 * bc];
         const float wx = P[3 * bc], wy = P[4 * bc], wz = P[5 * bc];
@@ -790,7 +840,7 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
     } else {
       rank = atomicAdd(&gcount[code], 1u);
     }
-    stag[i] = code | (rank << 5);
+    stag[i] = (Tag)(code | (rank << 5));
   }
   if (g.obs) {
     const int w = tid >> 5;
@@ -798,17 +848,25 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
       long long vals[16] = {o_q[0], o_q[1], o_q[2], o_q[3], o_q[4], o_q[5], o_q[6], o_q[7],
                             o_q[8], o_q[9], o_q[10], o_q[11], o_q[12], 0, 0, 0};
       const long long s = warp_reduce_scatter16(vals, lane);
-      if (!(lane & 1) && (lane >> 1) < 13) sh.obs.q[w][lane >> 1] = s;
+      if (!(lane & 1) && (lane >> 1) < 13) sobs.q[w][lane >> 1] = s;
     } else {
       float vals[16] = {o_px, o_py, o_pz, o_e, o_kxy, o_kyz, o_kzx, o_c[0], o_c[1], o_c[2],
                         o_c[3], o_c[4], o_c[5], 0.f, 0.f, 0.f};
       const float s = warp_reduce_scatter16(vals, lane);
-      if (!(lane & 1) && (lane >> 1) < 13) sh.obs.f[w][lane >> 1] = s;
+      if (!(lane & 1) && (lane >> 1) < 13) sobs.f[w][lane >> 1] = s;
     }
   }
+  // the ids come back into the stage (member lists and cell parameters, read above)
+  // through the async proxy
+  fence_proxy_async_smem();
   __syncthreads();
 
-  // ---- 5. reserve space in the destination bricks ----
+  // ---- 5. reserve space in the destination bricks; copy the ids back in meanwhile ----
+  if (tid == 0) {
+    const uint32_t bytes = (uint32_t)(((cnt + 3) & ~3) * 4);
+    mbar_expect_tx(&sh.bar, bytes);
+    if (bytes) bulk_g2s(sid, a.buf[par].id + (size_t)b * cap, bytes, &sh.bar);
+  }
   if (tid < 27 && gcount[tid] > 0) {
     const int dxb = tid % 3 - 1, dyb = (tid / 3) % 3 - 1, dzb = tid / 9 - 1;
     int qx = bx + dxb, qy = by + dyb, qz = bz + dzb;
@@ -825,15 +883,25 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
     if constexpr (DET) {
       // integer partials: the order of the atomics does not matter
       long long s = 0;
-      for (int w = 0; w < kThreads / 32; ++w) s += sh.obs.q[w][q];
+      for (int w = 0; w < kThreads / 32; ++w) s += sobs.q[w][q];
       atomicAdd(reinterpret_cast<unsigned long long*>(slot), (unsigned long long)s);
     } else {
       double s = 0.0;
-      for (int w = 0; w < kThreads / 32; ++w) s += (double)sh.obs.f[w][q];
+      for (int w = 0; w < kThreads / 32; ++w) s += (double)sobs.f[w][q];
       atomicAdd(slot, s);
     }
   }
   __syncthreads();
+
+  {
+    const bool ok = mbar_wait(&sh.bar, phase);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicOr(&a.ctrl->errors, kErrTimeout);
+      if (!ok) mbar_wait(&sh.bar, phase);
+      return false;
+    }
+    phase ^= 1u;
+  }
 
   // ---- 6. write out: each particle to its reserved slot ----
   for (int i = tid; i < cnt; i += kThreads) {
@@ -875,9 +943,14 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
 
 // --- kernels -------------------------------------------------------------------------
 
+// CTAs per SM the default bricks fit in shared memory (27.9 KB SRD, 29.2 KB SRD+a,
+// 37.8 KB AT+a per CTA); the register budget is held to match.
+template <int VAR>
+constexpr int kMinBlocks = VAR == 1 ? 6 : 8;
+
 // One box: one CTA per brick.
 template <int VAR, bool DET, int TIER>
-__global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks<VAR>) k_step(const StepArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ BrickShared sh;
   uint32_t phase = 0;
@@ -891,7 +964,7 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
 // packed boxes, box k owning items [begin[k], begin[k+1])) from a counter that is zero
 // at launch; each CTA's claims increase, so its box index only moves forward.
 template <int VAR, bool DET, int TIER>
-__global__ void __launch_bounds__(kThreads) k_step_packed(const __grid_constant__ PackTable p) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks<VAR>) k_step_packed(const __grid_constant__ PackTable p) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ BrickShared sh;
   __shared__ int s_w;
@@ -989,7 +1062,6 @@ cudaError_t set_cap_tiers(int v) {
 // occupancy), so boxes with different needs never lower each other's cap.
 cudaError_t configure_step_kernels(size_t max_dynamic_smem) {
   const int v = (int)max_dynamic_smem;
-  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = set_cap_tiers<0, false>(v);
   if (e == cudaSuccess) e = set_cap_tiers<1, false>(v);
