@@ -60,9 +60,20 @@ __device__ __forceinline__ float2 normal2(uint32_t ra, uint32_t rb) {
   return make_float2(R * c, R * s);
 }
 
-// the first (cosine) normal of the Box-Muller pair alone
-__device__ __forceinline__ float normal_cos(uint32_t ra, uint32_t rb) {
-  return sqrtf(-2.0f * logf(u01(ra))) * cospif(2.0f * u01(rb));
+// The three AT+a random-velocity normals from one Philox draw: the Box-Muller pair of
+// (r.x, r.y) and the cosine normal of (r.z, r.w), with the radius from the accurate
+// logarithm (its argument comes close to 1) and the angle evaluated as
+// -cos / -sin of pi (2u - 1) in [-pi, pi) by the hardware approximations (absolute
+// error below 6e-7, so below 3.5e-6 in a normal, whose radius stays under 5.8); the
+// square root as y rsqrt(y), y > 0.  These values decide no integer.
+__device__ __forceinline__ float3 normal3_at(uint4 r) {
+  constexpr float kPi = 3.14159265358979f;
+  const float y0 = -2.0f * logf(u01(r.x)), y1 = -2.0f * logf(u01(r.z));
+  const float R0 = y0 * rsqrtf(y0), R1 = y1 * rsqrtf(y1);
+  float s, c;
+  __sincosf(kPi * (2.0f * u01(r.y) - 1.0f), &s, &c);
+  const float c1 = __cosf(kPi * (2.0f * u01(r.w) - 1.0f));
+  return make_float3(-R0 * c, -R0 * s, -R1 * c1);
 }
 
 // Gamma(shape a >= 1, scale 1), Marsaglia & Tsang (ACM TOMS 26, 2000); attempt k uses

@@ -43,8 +43,8 @@ struct CellParams<0> {  // SRD: v_cm (3), rotation axis (3), kappa
   static constexpr bool kStoresRandomVelocity = false;
 };
 template <>
-struct CellParams<1> {  // AT+a: <w> = v_cm - <v_ran> (3), omega (3), rho_cm (3)
-  static constexpr int kParams = 9;
+struct CellParams<1> {  // AT+a: <w> - omega x rho_cm (3) with <w> = v_cm - <v_ran>, omega (3)
+  static constexpr int kParams = 6;
   static constexpr bool kStoresRandomVelocity = true;
 };
 template <>
@@ -461,10 +461,8 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
     if (g.debug) sgc[i] = (uint32_t)cx + (uint32_t)g.Lc[0] * ((uint32_t)cy + (uint32_t)g.Lc[1] * (uint32_t)cz);
     if constexpr (VAR == 1) {
       // AT+a: keep v_ran and w = v - v_ran
-      const uint4 r = draw(g, sid[i], step, kTagAtVel, 0u);
-      const float2 n01 = normal2(r.x, r.y);
-      const float n2 = normal_cos(r.z, r.w);
-      const float ux = g.sigma * n01.x, uy = g.sigma * n01.y, uz = g.sigma * n2;
+      const float3 n = normal3_at(draw(g, sid[i], step, kTagAtVel, 0u));
+      const float ux = g.sigma * n.x, uy = g.sigma * n.y, uz = g.sigma * n.z;
       sux[i] = ux; suy[i] = uy; suz[i] = uz;
       vx -= ux; vy -= uy; vz -= uz;
     }
@@ -724,7 +722,15 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
           float* P = spar + lc;
           P[0 * bc] = wmx; P[1 * bc] = wmy; P[2 * bc] = wmz;
           P[3 * bc] = ox_; P[4 * bc] = oy_; P[5 * bc] = oz_;
-          P[6 * bc] = rcx; P[7 * bc] = rcy; P[8 * bc] = rcz;
+          if constexpr (VAR == 1) {
+            // omega x (rho - rho_cm) = omega x rho - omega x rho_cm: the second term
+            // joins the cell's velocity offset
+            P[0 * bc] = wmx - (oy_ * rcz - oz_ * rcy);
+            P[1 * bc] = wmy - (oz_ * rcx - ox_ * rcz);
+            P[2 * bc] = wmz - (ox_ * rcy - oy_ * rcx);
+          } else {
+            P[6 * bc] = rcx; P[7 * bc] = rcy; P[8 * bc] = rcz;
+          }
           if constexpr (VAR == 2) {
             P[9 * bc] = ax; P[10 * bc] = ay; P[11 * bc] = az;
           }
@@ -787,11 +793,10 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
       nx = vbx; ny = vby; nz = vbz;
       if (lc != kNoCell) {
         const float* P = spar + lc;
-        const float rx = px - P[6 * bc], ry = py - P[7 * bc], rz = pz - P[8 * bc];
         const float wx = P[3 * bc], wy = P[4 * bc], wz = P[5 * bc];
-        nx = P[0] + ux + (wy * rz - wz * ry);
-        ny = P[bc] + uy + (wz * rx - wx * rz);
-        nz = P[2 * bc] + uz + (wx * ry - wy * rx);
+        nx = P[0] + ux + (wy * pz - wz * py);
+        ny = P[bc] + uy + (wz * px - wx * pz);
+        nz = P[2 * bc] + uz + (wx * py - wy * px);
       }
     }
     if (g.obs) {
