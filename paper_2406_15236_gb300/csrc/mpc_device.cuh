@@ -60,15 +60,26 @@ __device__ __forceinline__ float2 normal2(uint32_t ra, uint32_t rb) {
   return make_float2(R * c, R * s);
 }
 
+// -2 ln u for u = (k + 1/2) 2^-23 in (0, 1).  With t = 1 - u (exact): for t >= 2^-7 the
+// hardware log2 (absolute error below 2^-22 on [0.5, 2), 2 ulp below 0.5), else the
+// series 2 (t + t^2/2 + t^3/3), whose truncation is below t^3/4 relative.  Absolute error
+// below 3.4e-7 + 2.5e-7 |result|.
+__device__ __forceinline__ float minus_2_log_u01(float u) {
+  const float t = 1.0f - u;
+  const float series = 2.0f * t * (1.0f + t * (0.5f + t * (1.0f / 3.0f)));
+  const float hw = -1.3862943611198906f * __log2f(u);  // -2 ln 2 log2(u)
+  return t < 0.0078125f ? series : hw;
+}
+
 // The three AT+a random-velocity normals from one Philox draw: the Box-Muller pair of
-// (r.x, r.y) and the cosine normal of (r.z, r.w), with the radius from the accurate
-// logarithm (its argument comes close to 1) and the angle evaluated as
-// -cos / -sin of pi (2u - 1) in [-pi, pi) by the hardware approximations (absolute
-// error below 6e-7, so below 3.5e-6 in a normal, whose radius stays under 5.8); the
-// square root as y rsqrt(y), y > 0.  These values decide no integer.
+// (r.x, r.y) and the cosine normal of (r.z, r.w).  The radius is sqrt(-2 ln u) as
+// y rsqrt(y) (y > 0: u < 1), the angle -cos / -sin of pi (2u - 1) in [-pi, pi) by the
+// hardware approximations (absolute error below 6e-7).  A normal is off by less than
+// 6e-6 in the worst case (radius 5.8, u = 2^-24) and ~1e-6 typically.  These values
+// decide no integer.
 __device__ __forceinline__ float3 normal3_at(uint4 r) {
   constexpr float kPi = 3.14159265358979f;
-  const float y0 = -2.0f * logf(u01(r.x)), y1 = -2.0f * logf(u01(r.z));
+  const float y0 = minus_2_log_u01(u01(r.x)), y1 = minus_2_log_u01(u01(r.z));
   const float R0 = y0 * rsqrtf(y0), R1 = y1 * rsqrtf(y1);
   float s, c;
   __sincosf(kPi * (2.0f * u01(r.y) - 1.0f), &s, &c);

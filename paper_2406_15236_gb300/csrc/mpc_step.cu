@@ -367,6 +367,8 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
   // ---- 1. load the brick: thread 0 reads the step, its limit, the halt flag and both
   // count slots in one round trip, then starts the bulk copies ----
   if (tid == 0) {
+    // the barrier's init fence goes first, with no memory operation of its own to wait for
+    if (!PERSIST) mbar_init(&sh.bar, 1);
     const int64_t st = *(volatile int64_t*)&a.ctrl->step;
     const int64_t lim = *(volatile int64_t*)&a.ctrl->limit;
     const int32_t halted = *(volatile int32_t*)&a.ctrl->halted;
@@ -379,8 +381,6 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
       const int p = (int)(st & 1);
       c = p ? c_odd : c_even;
       if (c > (uint32_t)cap) c = cap;
-      a.cnt[p][b] = 0;  // this buffer becomes the destination of the next step
-      if (!PERSIST) mbar_init(&sh.bar, 1);
       const uint32_t bytes = (uint32_t)(((c + 3) & ~3u) * 4);
       // AT+a draws its random velocities from the ids now; the other variants need the
       // ids only for the write-out, copied in again then (step 5)
@@ -397,6 +397,7 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
         if (VAR == 1) bulk_g2s(sid, sb.id + off, bytes, &sh.bar);
         else bulk_prefetch_l2(sb.id + off, bytes);
       }
+      a.cnt[p][b] = 0;  // this buffer becomes the destination of the next step
     }
     sh.cnt = c;
   }
