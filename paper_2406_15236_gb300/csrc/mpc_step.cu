@@ -436,6 +436,13 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
   const int by = (b / g.nb[0]) % g.nb[1];
   const int bz = b / (g.nb[0] * g.nb[1]);
   const int ox = bx << Bs0, oy = by << Bs1, oz = bz << Bs2;
+  // bricks whose lower neighbour exists and whose upper neighbour is a whole brick inside
+  // the box, on every axis: the cells a particle of this brick can reach within one brick
+  // need no periodic wrap, so brick deltas follow from one shift per axis (a ragged box's
+  // partial last brick is too narrow for that: one step past it wraps to cell 0)
+  const bool inner = TIER > 0 && bx >= 1 && ((bx + 2) << Bs0) <= g.Lc[0] && by >= 1 &&
+                     ((by + 2) << Bs1) <= g.Lc[1] && bz >= 1 && ((bz + 2) << Bs2) <= g.Lc[2];
+  const uint32_t Ox = (uint32_t)ox << g.F, Oy = (uint32_t)oy << g.F, Oz = (uint32_t)oz << g.F;
 
   // ---- 2. rank each particle within its collision cell ----
   // Stored positions are already streamed for this step (the previous step streamed
@@ -446,9 +453,15 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
     const uint32_t x = sx[i], y = sy[i], z = zraw & ~kCrossedBit;
     float vx = svx[i], vy = svy[i], vz = svz[i];
     collision_velocity(g, zraw, vx, vy, vz);
-    const int cx = cell_axis(g, x, S0x, 0), cy = cell_axis(g, y, S0y, 1),
-              cz = cell_axis(g, z, S0z, 2);
-    const int lx = cx - ox, ly = cy - oy, lz = cz - oz;
+    int cx = 0, cy = 0, cz = 0, lx, ly, lz;
+    if (inner) {
+      lx = (int)(x + S0x - Ox) >> g.F;
+      ly = (int)(y + S0y - Oy) >> g.F;
+      lz = (int)(z + S0z - Oz) >> g.F;
+    } else {
+      cx = cell_axis(g, x, S0x, 0); cy = cell_axis(g, y, S0y, 1); cz = cell_axis(g, z, S0z, 2);
+      lx = cx - ox; ly = cy - oy; lz = cz - oz;
+    }
     uint32_t lcr;
     if ((unsigned)lx < (unsigned)B0 && (unsigned)ly < (unsigned)B1 &&
         (unsigned)lz < (unsigned)B2) {
@@ -612,6 +625,9 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
         // angular-momentum-conserving variants.  First pass: centre of mass and mean of
         // w (AT+a: w = v - v_ran; SRD+a: w = v, so the mean is v_cm)
         float r0 = 0.f, r1 = 0.f, r2 = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f;
+        constexpr bool kOnePass = VAR == 1 && !DET;
+        constexpr int kOnePassMin = 6;
+        float o_m[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if constexpr (DET) {
           // positions sum exactly as integers; velocities in fixed point
           long long R0 = 0, R1 = 0, R2 = 0, W0 = 0, W1 = 0, W2 = 0;
@@ -631,16 +647,31 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
         } else {
           for (int k = sub; k < n; k += tpc) {
             const int i = sperm[base + k];
-            r0 += rho_axis(g, sx[i], S0x); r1 += rho_axis(g, sy[i], S0y);
-            r2 += rho_axis(g, sz[i] & ~kCrossedBit, S0z);
-            w0 += svx[i]; w1 += svy[i]; w2 += svz[i];
+            const float px = rho_axis(g, sx[i], S0x), py = rho_axis(g, sy[i], S0y),
+                        pz = rho_axis(g, sz[i] & ~kCrossedBit, S0z);
+            const float vx = svx[i], vy = svy[i], vz = svz[i];
+            r0 += px; r1 += py; r2 += pz;
+            w0 += vx; w1 += vy; w2 += vz;
+            if constexpr (kOnePass) {
+              o_m[0] += px * px; o_m[1] += py * py; o_m[2] += pz * pz;
+              o_m[3] += px * py; o_m[4] += py * pz; o_m[5] += pz * px;
+              o_m[6] += py * vz - pz * vy; o_m[7] += pz * vx - px * vz; o_m[8] += px * vy - py * vx;
+            }
           }
           r0 = group_sum(r0, tpc); r1 = group_sum(r1, tpc); r2 = group_sum(r2, tpc);
           w0 = group_sum(w0, tpc); w1 = group_sum(w1, tpc); w2 = group_sum(w2, tpc);
+          if constexpr (kOnePass) {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) o_m[q] = group_sum(o_m[q], tpc);
+          }
         }
         const float inv = 1.0f / fmaxf((float)n, 1.0f);
         const float rcx = r0 * inv, rcy = r1 * inv, rcz = r2 * inv;
         const float wmx = w0 * inv, wmy = w1 * inv, wmz = w2 * inv;
+        // cells of kOnePassMin or more members take their moments from the raw sums;
+        // the smaller ones (where a near-degenerate configuration is likelier) take the
+        // second pass
+        const bool second = !kOnePass || n < kOnePassMin;
         // SRD+a: the cell's random rotation axis (every lane of the group draws it)
         float ax = 0.f, ay = 0.f, az = 0.f;
         if constexpr (VAR == 2) {
@@ -657,7 +688,9 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
         float Mxx = 0.f, Myy = 0.f, Mzz = 0.f, Mxy = 0.f, Myz = 0.f, Mzx = 0.f;
         float Lx = 0.f, Ly = 0.f, Lz = 0.f;
         long long qM[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // deterministic mode
-        for (int k = sub; k < n; k += tpc) {
+        const bool any_second = !kOnePass || __any_sync(0xffffffffu, second && n > 0);
+        const int n2 = second ? n : 0;
+        for (int k = sub; any_second && k < n2; k += tpc) {
           const int i = sperm[base + k];
           const float rx = rho_axis(g, sx[i], S0x) - rcx, ry = rho_axis(g, sy[i], S0y) - rcy,
                       rz = rho_axis(g, sz[i] & ~kCrossedBit, S0z) - rcz;
@@ -689,9 +722,19 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
           Mxy = from_fx(qM[3]); Myz = from_fx(qM[4]); Mzx = from_fx(qM[5]);
           Lx = from_fx(qM[6]); Ly = from_fx(qM[7]); Lz = from_fx(qM[8]);
         } else {
-          Mxx = group_sum(Mxx, tpc); Myy = group_sum(Myy, tpc); Mzz = group_sum(Mzz, tpc);
-          Mxy = group_sum(Mxy, tpc); Myz = group_sum(Myz, tpc); Mzx = group_sum(Mzx, tpc);
-          Lx = group_sum(Lx, tpc); Ly = group_sum(Ly, tpc); Lz = group_sum(Lz, tpc);
+          if (any_second) {
+            Mxx = group_sum(Mxx, tpc); Myy = group_sum(Myy, tpc); Mzz = group_sum(Mzz, tpc);
+            Mxy = group_sum(Mxy, tpc); Myz = group_sum(Myz, tpc); Mzx = group_sum(Mzx, tpc);
+            Lx = group_sum(Lx, tpc); Ly = group_sum(Ly, tpc); Lz = group_sum(Lz, tpc);
+          }
+          if (!second) {
+            const float fn = (float)n;
+            Mxx = o_m[0] - fn * rcx * rcx; Myy = o_m[1] - fn * rcy * rcy; Mzz = o_m[2] - fn * rcz * rcz;
+            Mxy = o_m[3] - fn * rcx * rcy; Myz = o_m[4] - fn * rcy * rcz; Mzx = o_m[5] - fn * rcz * rcx;
+            Lx = o_m[6] - fn * (rcy * wmz - rcz * wmy);
+            Ly = o_m[7] - fn * (rcz * wmx - rcx * wmz);
+            Lz = o_m[8] - fn * (rcx * wmy - rcy * wmx);
+          }
         }
         if (exists && n > 0 && sub == 0) {
           const float tr = Mxx + Myy + Mzz;
@@ -822,15 +865,25 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
     sx[i] = x; sy[i] = y; sz[i] = z;
     svx[i] = nx; svy[i] = ny; svz[i] = nz;
     const uint32_t zs = z & ~kCrossedBit;
-    const int qx = cell_axis(g, x, S1x, 0) >> Bs0;
-    const int qy = cell_axis(g, y, S1y, 1) >> Bs1;
-    const int qz = cell_axis(g, zs, S1z, 2) >> Bs2;
-    const int dxb = brick_delta(qx, bx, g.nb[0], true);
-    const int dyb = brick_delta(qy, by, g.nb[1], true);
-    const int dzb = brick_delta(qz, bz, g.nb[2], zper);
-    const uint32_t code = (dxb == 9 || dyb == 9 || dzb == 9)
-                              ? 27u
-                              : (uint32_t)((dxb + 1) + 3 * (dyb + 1) + 9 * (dzb + 1));
+    uint32_t code;
+    if (inner) {
+      const int dxb = (int)(x + S1x - Ox) >> (g.F + Bs0);
+      const int dyb = (int)(y + S1y - Oy) >> (g.F + Bs1);
+      const int dzb = (int)(zs + S1z - Oz) >> (g.F + Bs2);
+      code = ((unsigned)(dxb + 1) > 2u || (unsigned)(dyb + 1) > 2u || (unsigned)(dzb + 1) > 2u)
+                 ? 27u
+                 : (uint32_t)((dxb + 1) + 3 * (dyb + 1) + 9 * (dzb + 1));
+    } else {
+      const int qx = cell_axis(g, x, S1x, 0) >> Bs0;
+      const int qy = cell_axis(g, y, S1y, 1) >> Bs1;
+      const int qz = cell_axis(g, zs, S1z, 2) >> Bs2;
+      const int dxb = brick_delta(qx, bx, g.nb[0], true);
+      const int dyb = brick_delta(qy, by, g.nb[1], true);
+      const int dzb = brick_delta(qz, bz, g.nb[2], zper);
+      code = (dxb == 9 || dyb == 9 || dzb == 9)
+                 ? 27u
+                 : (uint32_t)((dxb + 1) + 3 * (dyb + 1) + 9 * (dzb + 1));
+    }
     // rank within the destination group: particles that stay in this brick (most of
     // them) get consecutive slots through one warp ballot, so their writes below are
     // contiguous runs; the others take a shared-memory atomic each

@@ -113,6 +113,16 @@ def test_ragged_box(variant, h):
     _run_parity(kw, 6, strict_flags=oracle.FLAG_DEGENERATE)
 
 
+@pytest.mark.parametrize("variant,h", [(0, 1.0), (1, 0.5)])
+def test_ragged_box_default_bricks(variant, h):
+    """N_c = 10 takes the compiled-in 4x4x4-cell bricks; 21 and 13 cells leave a last brick
+    one cell wide, so a particle that streams a cell and a half past the brick before it
+    wraps to cell 0 (the brick-delta shortcut of interior bricks must not apply there).
+    Large time steps make such moves common."""
+    kw = dict(L=(21, 18, 13), n_c=10.0, h=h, alpha_deg=130.0, variant=variant, seed=14)
+    _run_parity(kw, 5, strict_flags=oracle.FLAG_DEGENERATE)
+
+
 def test_sparse_cells_at_a():
     """N_c = 1.5: many cells hold 0, 1 or 2 particles (pair pseudo-inverse branch)."""
     kw = dict(L=10, n_c=1.5, h=0.05, variant=1, seed=12)
