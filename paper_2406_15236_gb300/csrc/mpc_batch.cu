@@ -180,7 +180,7 @@ void arena_release(void* ctx, void* p, size_t bytes, void* stream) {
 }
 
 constexpr int kTableBuffers = 3;  // pinned host copies of the member table in rotation
-constexpr int kBranches = 4;      // concurrent streams for the launches of one step
+constexpr int kBranches = 2;      // concurrent streams for the launches of one step
 constexpr int kSoloWaves = 2;     // members with this many waves of bricks run solo
 constexpr int kWaveCtasPerSm = 6; // CTAs per SM of a wave (the AT+a kernel's occupancy)
 
