@@ -100,6 +100,11 @@ def lib():
             L.orc_stream_one.argtypes = [P(Params), P(u32), P(f64)]
             L.orc_min_eigenvalue_sym3.argtypes = [P(f64)]
             L.orc_min_eigenvalue_sym3.restype = f64
+            L.orc_cell_omega.argtypes = [i64, P(f64), P(f64), P(f64), P(f64), P(f64)]
+            L.orc_cell_omega.restype = ctypes.c_int
+            L.orc_phantoms.argtypes = [P(Params), i64, u32, f64, ctypes.c_int, P(f64), P(f64),
+                                       P(f64)]
+            L.orc_phantoms.restype = ctypes.c_int
             L.orc_sample_normal.argtypes = [ctypes.c_uint64, i64, P(f64)]
             L.orc_sample_gamma.argtypes = [ctypes.c_uint64, f64, i64, P(f64)]
             L.orc_sample_poisson.argtypes = [ctypes.c_uint64, f64, i64, P(ctypes.c_int32)]
@@ -234,6 +239,32 @@ def stream_one(p: Params, x, v):
 def min_eigenvalue_sym3(A) -> float:
     a = np.ascontiguousarray(A, dtype=np.float64).reshape(9)
     return lib().orc_min_eigenvalue_sym3(_ptr(a, ctypes.c_double))
+
+
+def cell_omega(rho, w):
+    """The angular-momentum restoring rotation of one cell (Eqs. 3-4): rho (n, 3) positions
+    relative to the cell centre, w (n, 3) the velocities whose angular momentum about the
+    centre of mass is restored.  Returns (omega, rcm, sens, flags)."""
+    r = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1, 3)
+    ww = np.ascontiguousarray(w, dtype=np.float64).reshape(-1, 3)
+    n = r.shape[0]
+    om, rc = np.zeros(3), np.zeros(3)
+    se = np.zeros(max(n, 1))
+    fl = lib().orc_cell_omega(n, _ptr(r, ctypes.c_double), _ptr(ww, ctypes.c_double),
+                              _ptr(om, ctypes.c_double), _ptr(rc, ctypes.c_double),
+                              _ptr(se, ctypes.c_double))
+    return om, rc, se[:n], fl
+
+
+def phantoms(p: Params, step_index: int, cell: int, phi: float, wall: int):
+    """Aggregate phantom particles of one wall-cut cell: (count, momentum[3], internal
+    kinetic energy, flags)."""
+    nph = np.zeros(1)
+    P = np.zeros(3)
+    K = np.zeros(1)
+    fl = lib().orc_phantoms(ctypes.byref(p), step_index, cell, phi, wall, _ptr(nph, ctypes.c_double),
+                            _ptr(P, ctypes.c_double), _ptr(K, ctypes.c_double))
+    return int(nph[0]), P, float(K[0]), fl
 
 
 def sample_normal(seed: int, n: int) -> np.ndarray:

@@ -418,6 +418,91 @@ static int solve_inertia(int64_t n, const double J[3][3], const double Lr[3],
   return flags;
 }
 
+/* The angular-momentum restoring rotation of one cell (Eqs. 3-4 for SRD+a; the same
+ * construction for AT+a): with r_j = rho_j - rho_cm the positions relative to the cell's
+ * centre of mass (unit masses), J = sum_j (|r_j|^2 1 - r_j r_j^T) the moment-of-inertia
+ * tensor and L = sum_j r_j x w_j the angular momentum the collision would otherwise
+ * change, omega = J^{-1} L.  rho, w: 3n values (particle-major); sens (n values or NULL):
+ * the float32 rounding sensitivity of each particle's new velocity (omega_sensitivity
+ * times |r_i|, plus 2|omega| for the rounding of r_i itself).  Returns cell flags. */
+int orc_cell_omega(int64_t n, const double* rho, const double* w, double omega[3],
+                   double rcm[3], double* sens) {
+  double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  double Lr[3] = {0, 0, 0};
+  double pair_axis[3] = {0, 0, 0};
+  double sum_rw = 0.0, sum_w = 0.0, sum_r = 0.0;
+  rcm[0] = rcm[1] = rcm[2] = 0.0;
+  omega[0] = omega[1] = omega[2] = 0.0;
+  if (n <= 0) return 0;
+  for (int64_t k = 0; k < n; ++k)
+    for (int a = 0; a < 3; ++a) rcm[a] += rho[3 * k + a];
+  for (int a = 0; a < 3; ++a) rcm[a] /= (double)n;
+  if (n == 2)
+    for (int a = 0; a < 3; ++a) pair_axis[a] = rho[a] - rho[3 + a];
+  for (int64_t k = 0; k < n; ++k) {
+    double r[3], rxw[3];
+    for (int a = 0; a < 3; ++a) r[a] = rho[3 * k + a] - rcm[a];
+    double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) J[a][b] += (a == b ? r2 : 0.0) - r[a] * r[b];
+    cross3(r, w + 3 * k, rxw);
+    for (int a = 0; a < 3; ++a) Lr[a] += rxw[a];
+    const double* wv = w + 3 * k;
+    double wn = sqrt(wv[0] * wv[0] + wv[1] * wv[1] + wv[2] * wv[2]);
+    sum_rw += sqrt(r2) * wn;
+    sum_w += wn;
+    sum_r += sqrt(r2);
+  }
+  int flags = solve_inertia(n, J, Lr, pair_axis, omega);
+  if (sens) {
+    double on = sqrt(omega[0] * omega[0] + omega[1] * omega[1] + omega[2] * omega[2]);
+    double sc = omega_sensitivity(n, J, pair_axis, sum_rw, sum_w, sum_r, on);
+    for (int64_t k = 0; k < n; ++k) {
+      double r[3];
+      for (int a = 0; a < 3; ++a) r[a] = rho[3 * k + a] - rcm[a];
+      sens[k] = sc * sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]) + 2.0 * on;
+    }
+  }
+  return flags;
+}
+
+/* Phantom particles of a wall-cut cell (Sec. II, "Boundary conditions"): the part of the
+ * cell inside the wall (volume fraction phi) is filled with virtual particles at the mean
+ * density, with Maxwell-Boltzmann velocities about the wall's own velocity.  Only their
+ * aggregates enter an SRD collision, so they are drawn as aggregates: the count
+ * k ~ Poisson(N_c phi); the total momentum, per component m k u_wall + N(0, k m kT); and
+ * Kint = sum m |v - <v>|^2 about their own mean velocity (twice their internal kinetic
+ * energy), kT chi^2(3(k - 1)), i.e. 2 kT times a Gamma(3(k - 1)/2) draw -- exact in
+ * distribution for k Gaussian velocities.  wall: 0 the
+ * wall at z = 0, 1 the wall at z = Lz.  Returns cell flags (near-tie decisions). */
+int orc_phantoms(const orc_params* p, int64_t step, uint32_t cell, double phi, int wall,
+                 double* nph, double P[3], double* Kint) {
+  const double m = p->m;
+  int flags = 0;
+  uint32_t r[4], r1[4];
+  draw(p, cell, (uint32_t)step, TAG_PHANTOM, 0u, r);
+  draw(p, cell, (uint32_t)step, TAG_PHANTOM, 1u, r1);
+  int tie = 0;
+  int32_t k = poisson_inv(uniform01(r[0]), p->n_c * phi, &tie);
+  if (tie) flags |= ORC_FLAG_POISSON_NEAR_TIE;
+  *nph = (double)k;
+  double zx, zy, zz, zdummy;
+  box_muller(uniform01(r[1]), uniform01(r[2]), &zx, &zy);
+  box_muller(uniform01(r1[0]), uniform01(r1[1]), &zz, &zdummy);
+  double sp = m * sqrt((double)k * p->kT / m);
+  /* phantoms move with their wall on average */
+  P[0] = sp * zx + m * (double)k * p->wall_u[wall];
+  P[1] = sp * zy;
+  P[2] = sp * zz;
+  *Kint = 0.0;
+  if (k >= 2) {
+    int t2 = 0;
+    *Kint = p->kT * 2.0 * gamma_mt(p, cell, (uint32_t)step, TAG_PHGAMMA, 1.5 * (double)(k - 1), &t2);
+    if (t2) flags |= ORC_FLAG_MBS_NEAR_TIE;
+  }
+  return flags;
+}
+
 /* ------------------------------------------------------------------------------ */
 
 int orc_init(const orc_params* p, int64_t N, uint32_t* X, double* V, uint32_t* id) {
@@ -514,29 +599,8 @@ int orc_step(const orc_params* p, int64_t N, uint32_t* X, double* V, const uint3
         double phi = -1.0;
         if (cz == 0) phi = s;
         else if (cz == p->L[2]) phi = 1.0 - s;
-        if (phi >= 0.0) {
-          uint32_t r[4], r1[4];
-          draw(p, (uint32_t)c, (uint32_t)step, TAG_PHANTOM, 0u, r);
-          draw(p, (uint32_t)c, (uint32_t)step, TAG_PHANTOM, 1u, r1);
-          int tie = 0;
-          int32_t k = poisson_inv(uniform01(r[0]), p->n_c * phi, &tie);
-          if (tie) flags |= ORC_FLAG_POISSON_NEAR_TIE;
-          nph = (double)k;
-          double zx, zy, zz, zdummy;
-          box_muller(uniform01(r[1]), uniform01(r[2]), &zx, &zy);
-          box_muller(uniform01(r1[0]), uniform01(r1[1]), &zz, &zdummy);
-          double sp = m * sqrt(nph * p->kT / m);
-          /* phantoms move with their wall on average */
-          Pph[0] = sp * zx + m * nph * p->wall_u[cz == 0 ? 0 : 1];
-          Pph[1] = sp * zy;
-          Pph[2] = sp * zz;
-          if (k >= 2) {
-            int t2 = 0;
-            Kint = p->kT * 2.0 * gamma_mt(p, (uint32_t)c, (uint32_t)step, TAG_PHGAMMA,
-                                          1.5 * (double)(k - 1), &t2);
-            if (t2) flags |= ORC_FLAG_MBS_NEAR_TIE;
-          }
-        }
+        if (phi >= 0.0)
+          flags |= orc_phantoms(p, step, (uint32_t)c, phi, cz == 0 ? 0 : 1, &nph, Pph, &Kint);
       }
       double ntot = (double)n + nph;
       double vcm[3];
@@ -576,108 +640,65 @@ int orc_step(const orc_params* p, int64_t N, uint32_t* X, double* V, const uint3
       }
     } else {
       /* angular-momentum-conserving variants: centre-of-mass frame of the cell */
-      double vcm[3], rcm[3] = {0, 0, 0};
+      double vcm[3];
       for (int a = 0; a < 3; ++a) vcm[a] = sumv[a] / (double)n;
+      double* rk = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+      double* wk = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+      double* dv = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+      double* sk = (double*)malloc(sizeof(double) * (size_t)n);
+      if (!rk || !wk || !dv || !sk) return -1;
       for (int64_t k = 0; k < n; ++k)
-        for (int a = 0; a < 3; ++a) rcm[a] += rho[3 * mem[k] + a];
-      for (int a = 0; a < 3; ++a) rcm[a] /= (double)n;
-      double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-      double Lr[3] = {0, 0, 0};
-      double pair_axis[3] = {0, 0, 0};
-      double sum_rw = 0.0, sum_w = 0.0, sum_r = 0.0;
-      if (n == 2)
-        for (int a = 0; a < 3; ++a) pair_axis[a] = rho[3 * mem[0] + a] - rho[3 * mem[1] + a];
-
+        for (int a = 0; a < 3; ++a) rk[3 * k + a] = rho[3 * mem[k] + a];
+      double vrm[3] = {0, 0, 0};
       if (p->variant == ORC_AT_A) {
         /* MPC-AT+a: v_i' = v_cm + v_i^ran - <v^ran> + omega x r_ic, with
-         * omega = J^{-1} sum_j r_jc x (v_j - v_j^ran), v^ran ~ N(0, kT/m) per component */
-        double* vran = (double*)malloc(sizeof(double) * 3 * (size_t)n);
-        double vrm[3] = {0, 0, 0};
+         * omega = J^{-1} sum_j r_jc x (v_j - v_j^ran), v^ran ~ N(0, kT/m) per component;
+         * dv holds v^ran */
         for (int64_t k = 0; k < n; ++k) {
           uint32_t r[4];
           draw(p, id[mem[k]], (uint32_t)step, TAG_ATV, 0u, r);
           double z0, z1, z2, z3;
           box_muller(uniform01(r[0]), uniform01(r[1]), &z0, &z1);
           box_muller(uniform01(r[2]), uniform01(r[3]), &z2, &z3);
-          vran[3 * k + 0] = sigma * z0;
-          vran[3 * k + 1] = sigma * z1;
-          vran[3 * k + 2] = sigma * z2;
-          for (int a = 0; a < 3; ++a) vrm[a] += vran[3 * k + a];
+          dv[3 * k + 0] = sigma * z0;
+          dv[3 * k + 1] = sigma * z1;
+          dv[3 * k + 2] = sigma * z2;
+          for (int a = 0; a < 3; ++a) vrm[a] += dv[3 * k + a];
         }
         for (int a = 0; a < 3; ++a) vrm[a] /= (double)n;
-        for (int64_t k = 0; k < n; ++k) {
-          int64_t i = mem[k];
-          double r[3], w[3], rxw[3];
-          for (int a = 0; a < 3; ++a) {
-            r[a] = rho[3 * i + a] - rcm[a];
-            w[a] = vb[3 * i + a] - vran[3 * k + a];
-          }
-          double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-          for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) J[a][b] += (a == b ? r2 : 0.0) - r[a] * r[b];
-          cross3(r, w, rxw);
-          for (int a = 0; a < 3; ++a) Lr[a] += rxw[a];
-          double wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
-          sum_rw += sqrt(r2) * wn;
-          sum_w += wn;
-          sum_r += sqrt(r2);
-        }
-        double omega[3];
-        flags |= solve_inertia(n, J, Lr, pair_axis, omega);
-        double on = sqrt(omega[0] * omega[0] + omega[1] * omega[1] + omega[2] * omega[2]);
-        double sens = sens_out ? omega_sensitivity(n, J, pair_axis, sum_rw, sum_w, sum_r, on) : 0.0;
-        for (int64_t k = 0; k < n; ++k) {
-          int64_t i = mem[k];
-          double r[3], wxr[3];
-          for (int a = 0; a < 3; ++a) r[a] = rho[3 * i + a] - rcm[a];
-          cross3(omega, r, wxr);
-          for (int a = 0; a < 3; ++a)
-            vnew[3 * i + a] = vcm[a] + vran[3 * k + a] - vrm[a] + wxr[a];
-          if (sens_out)
-            sens_out[i] = sens * sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]) + 2.0 * on;
-        }
-        free(vran);
+        for (int64_t k = 0; k < n; ++k)
+          for (int a = 0; a < 3; ++a) wk[3 * k + a] = vb[3 * mem[k] + a] - dv[3 * k + a];
       } else {
         /* MPC-SRD+a, Eqs. (3)-(4): v_i' = v_cm + D v_ic + omega x r_ic with
-         * omega = m I^{-1} sum_i r_ic x (v_ic - D v_ic) */
+         * omega = m I^{-1} sum_i r_ic x (v_ic - D v_ic); dv holds D v_ic */
         double axis[3];
         orc_srd_axis(p, step, (uint32_t)c, axis);
-        double* dv = (double*)malloc(sizeof(double) * 3 * (size_t)n);
         for (int64_t k = 0; k < n; ++k) {
-          int64_t i = mem[k];
-          double vic[3], rot[3], r[3], w[3], rxw[3];
-          for (int a = 0; a < 3; ++a) vic[a] = vb[3 * i + a] - vcm[a];
+          double vic[3], rot[3];
+          for (int a = 0; a < 3; ++a) vic[a] = vb[3 * mem[k] + a] - vcm[a];
           orc_rotate(axis, alpha, vic, rot);
           for (int a = 0; a < 3; ++a) {
             dv[3 * k + a] = rot[a];
-            r[a] = rho[3 * i + a] - rcm[a];
-            w[a] = vic[a] - rot[a];
+            wk[3 * k + a] = vic[a] - rot[a];
           }
-          double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-          for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) J[a][b] += (a == b ? r2 : 0.0) - r[a] * r[b];
-          cross3(r, w, rxw);
-          for (int a = 0; a < 3; ++a) Lr[a] += rxw[a];
-          double wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
-          sum_rw += sqrt(r2) * wn;
-          sum_w += wn;
-          sum_r += sqrt(r2);
         }
-        double omega[3];
-        flags |= solve_inertia(n, J, Lr, pair_axis, omega);
-        double on = sqrt(omega[0] * omega[0] + omega[1] * omega[1] + omega[2] * omega[2]);
-        double sens = sens_out ? omega_sensitivity(n, J, pair_axis, sum_rw, sum_w, sum_r, on) : 0.0;
-        for (int64_t k = 0; k < n; ++k) {
-          int64_t i = mem[k];
-          double r[3], wxr[3];
-          for (int a = 0; a < 3; ++a) r[a] = rho[3 * i + a] - rcm[a];
-          cross3(omega, r, wxr);
-          for (int a = 0; a < 3; ++a) vnew[3 * i + a] = vcm[a] + dv[3 * k + a] + wxr[a];
-          if (sens_out)
-            sens_out[i] = sens * sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]) + 2.0 * on;
-        }
-        free(dv);
       }
+      double omega[3], rcm[3];
+      flags |= orc_cell_omega(n, rk, wk, omega, rcm, sens_out ? sk : NULL);
+      for (int64_t k = 0; k < n; ++k) {
+        int64_t i = mem[k];
+        double r[3], wxr[3];
+        for (int a = 0; a < 3; ++a) r[a] = rk[3 * k + a] - rcm[a];
+        cross3(omega, r, wxr);
+        for (int a = 0; a < 3; ++a) {
+          if (p->variant == ORC_AT_A)
+            vnew[3 * i + a] = vcm[a] + dv[3 * k + a] - vrm[a] + wxr[a];
+          else
+            vnew[3 * i + a] = vcm[a] + dv[3 * k + a] + wxr[a];
+        }
+        if (sens_out) sens_out[i] = sk[k];
+      }
+      free(rk); free(wk); free(dv); free(sk);
     }
     if (cell_flags) cell_flags[c] = (uint8_t)flags;
   }

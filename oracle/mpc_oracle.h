@@ -76,6 +76,10 @@ void orc_srd_axis(const orc_params* p, int64_t step, uint32_t cell, double axis[
 void orc_rotate(const double axis[3], double alpha_rad, const double v[3], double out[3]);
 void orc_stream_one(const orc_params* p, uint32_t x[3], double v[3]);
 double orc_min_eigenvalue_sym3(const double A[9]);
+int orc_cell_omega(int64_t n, const double* rho, const double* w, double omega[3],
+                   double rcm[3], double* sens);
+int orc_phantoms(const orc_params* p, int64_t step, uint32_t cell, double phi, int wall,
+                 double* nph, double P[3], double* Kint);
 void orc_sample_normal(uint64_t seed, int64_t n, double* out);
 void orc_sample_gamma(uint64_t seed, double shape, int64_t n, double* out);
 void orc_sample_poisson(uint64_t seed, double lambda, int64_t n, int32_t* out);
