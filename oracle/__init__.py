@@ -100,6 +100,8 @@ def lib():
             L.orc_stream_one.argtypes = [P(Params), P(u32), P(f64)]
             L.orc_min_eigenvalue_sym3.argtypes = [P(f64)]
             L.orc_min_eigenvalue_sym3.restype = f64
+            L.orc_max_eigenvalue_sym3.argtypes = [P(f64)]
+            L.orc_max_eigenvalue_sym3.restype = f64
             L.orc_cell_omega.argtypes = [i64, P(f64), P(f64), P(f64), P(f64), P(f64)]
             L.orc_cell_omega.restype = ctypes.c_int
             L.orc_phantoms.argtypes = [P(Params), i64, u32, f64, ctypes.c_int, P(f64), P(f64),
@@ -265,6 +267,15 @@ def phantoms(p: Params, step_index: int, cell: int, phi: float, wall: int):
     fl = lib().orc_phantoms(ctypes.byref(p), step_index, cell, phi, wall, _ptr(nph, ctypes.c_double),
                             _ptr(P, ctypes.c_double), _ptr(K, ctypes.c_double))
     return int(nph[0]), P, float(K[0]), fl
+
+
+def max_eigenvalue_sym3(A) -> float:
+    a = np.ascontiguousarray(A, dtype=np.float64).reshape(9)
+    return lib().orc_max_eigenvalue_sym3(_ptr(a, ctypes.c_double))
+
+
+COND_FLOAT32 = 20.0  # cond(J) above which a cell is flagged FLAG_ILL_CONDITIONED
+TIGHT_RMS = 0.05  # rms radius below which a cell of n >= 2 is flagged FLAG_ILL_CONDITIONED
 
 
 def sample_normal(seed: int, n: int) -> np.ndarray:

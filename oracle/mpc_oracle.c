@@ -331,16 +331,21 @@ static void cross3(const double a[3], const double b[3], double out[3]) {
   out[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-/* smallest eigenvalue of a symmetric 3x3 matrix, closed form of O. K. Smith,
- * "Eigenvalues of a symmetric 3x3 matrix", CACM 4 (1961) */
-static double min_eigenvalue_sym3(const double A[3][3]) {
+/* smallest and largest eigenvalue of a symmetric 3x3 matrix, closed form of O. K. Smith,
+ * "Eigenvalues of a symmetric 3x3 matrix", CACM 4 (1961): with q = tr(A)/3 and
+ * B = (A - q 1)/p, the eigenvalues are q + 2 p cos(phi + 2 pi k/3), phi = acos(det(B)/2)/3 */
+static void eigen_extremes_sym3(const double A[3][3], double* lmin, double* lmax) {
   double p1 = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
   double q = (A[0][0] + A[1][1] + A[2][2]) / 3.0;
   if (p1 == 0.0) {
-    double m = A[0][0];
-    if (A[1][1] < m) m = A[1][1];
-    if (A[2][2] < m) m = A[2][2];
-    return m;
+    double lo = A[0][0], hi = A[0][0];
+    for (int a = 1; a < 3; ++a) {
+      if (A[a][a] < lo) lo = A[a][a];
+      if (A[a][a] > hi) hi = A[a][a];
+    }
+    *lmin = lo;
+    *lmax = hi;
+    return;
   }
   double p2 = (A[0][0] - q) * (A[0][0] - q) + (A[1][1] - q) * (A[1][1] - q) +
               (A[2][2] - q) * (A[2][2] - q) + 2.0 * p1;
@@ -355,7 +360,14 @@ static double min_eigenvalue_sym3(const double A[3][3]) {
   if (r < -1.0) r = -1.0;
   if (r > 1.0) r = 1.0;
   double phi = acos(r) / 3.0;
-  return q + 2.0 * pp * cos(phi + 2.0 * M_PI / 3.0);
+  *lmax = q + 2.0 * pp * cos(phi);
+  *lmin = q + 2.0 * pp * cos(phi + 2.0 * M_PI / 3.0);
+}
+
+static double min_eigenvalue_sym3(const double A[3][3]) {
+  double lo, hi;
+  eigen_extremes_sym3(A, &lo, &hi);
+  return lo;
 }
 
 /* First-order sensitivity of the new velocities to float32 rounding in the cell's
@@ -386,13 +398,16 @@ static int solve_inertia(int64_t n, const double J[3][3], const double Lr[3],
                          const double pair_axis[3], double omega[3]) {
   omega[0] = omega[1] = omega[2] = 0.0;
   if (n <= 1) return 0;
+  /* members within ORC_TIGHT_RMS of their centre of mass: see ORC_FLAG_ILL_CONDITIONED */
+  const double trM = 0.5 * (J[0][0] + J[1][1] + J[2][2]);
+  const int tight = trM < ORC_TIGHT_RMS * ORC_TIGHT_RMS * (double)n ? ORC_FLAG_ILL_CONDITIONED : 0;
   if (n == 2) {
     double d2 = pair_axis[0] * pair_axis[0] + pair_axis[1] * pair_axis[1] +
                 pair_axis[2] * pair_axis[2];
     if (d2 <= 0.0) return ORC_FLAG_DEGENERATE;
     double dl = (pair_axis[0] * Lr[0] + pair_axis[1] * Lr[1] + pair_axis[2] * Lr[2]) / d2;
     for (int a = 0; a < 3; ++a) omega[a] = (2.0 / d2) * (Lr[a] - pair_axis[a] * dl);
-    return 0;
+    return tight;
   }
   double A[3][3];
   A[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
@@ -406,13 +421,10 @@ static int solve_inertia(int64_t n, const double J[3][3], const double Lr[3],
   A[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
   double det = J[0][0] * A[0][0] + J[0][1] * A[1][0] + J[0][2] * A[2][0];
   if (!(det > 0.0)) return ORC_FLAG_DEGENERATE;
-  double nJ = 0.0, nA = 0.0;
-  for (int a = 0; a < 3; ++a)
-    for (int b = 0; b < 3; ++b) {
-      nJ += J[a][b] * J[a][b];
-      nA += A[a][b] * A[a][b];
-    }
-  int flags = (sqrt(nJ) * sqrt(nA) / det > 1e3) ? ORC_FLAG_ILL_CONDITIONED : 0;
+  /* ill-conditioned for a float32 solve: see ORC_FLAG_ILL_CONDITIONED */
+  double lo, hi;
+  eigen_extremes_sym3(J, &lo, &hi);
+  int flags = (!(lo > 0.0) || hi > ORC_COND_FLOAT32 * lo) ? ORC_FLAG_ILL_CONDITIONED : tight;
   for (int a = 0; a < 3; ++a)
     omega[a] = (A[a][0] * Lr[0] + A[a][1] * Lr[1] + A[a][2] * Lr[2]) / det;
   return flags;
@@ -750,6 +762,13 @@ int orc_step(const orc_params* p, int64_t N, uint32_t* X, double* V, const uint3
 double orc_min_eigenvalue_sym3(const double A[9]) {
   double M[3][3] = {{A[0], A[1], A[2]}, {A[3], A[4], A[5]}, {A[6], A[7], A[8]}};
   return min_eigenvalue_sym3(M);
+}
+
+double orc_max_eigenvalue_sym3(const double A[9]) {
+  double M[3][3] = {{A[0], A[1], A[2]}, {A[3], A[4], A[5]}, {A[6], A[7], A[8]}};
+  double lo, hi;
+  eigen_extremes_sym3(M, &lo, &hi);
+  return hi;
 }
 
 /* ------------------------------------------------------------------------------ */

@@ -45,9 +45,24 @@ typedef struct {
 enum {
   ORC_FLAG_MBS_NEAR_TIE = 1,   /* a Marsaglia-Tsang decision was within 1e-5 of its threshold */
   ORC_FLAG_POISSON_NEAR_TIE = 2,
-  ORC_FLAG_ILL_CONDITIONED = 4, /* angular-momentum solve with cond(J) > 1e3 */
+  /* angular-momentum solve that float32 arithmetic cannot take to the 1e-5 velocity bar;
+   * there the float32 result is good only to its first-order sensitivity (sens_out):
+   * (a) n >= 3 and cond(J) = lambda_max / lambda_min > ORC_COND_FLOAT32.  A float32 solve
+   *     rounds the entries of J by a relative u = 2^-24; that moves omega by ~u cond
+   *     |omega|, and where L points along the weak axis omega itself grows like cond, so
+   *     a member's velocity error grows like u cond^2 |L| |r| / lambda_max (about
+   *     1e-7 cond^2 / sqrt(n) in unit-temperature cells): below 1e-5 up to cond = 20.
+   *     About 0.2 % of the cells at N_c = 10.
+   * (b) n >= 2 members within ORC_TIGHT_RMS (rms) of their centre of mass.  Positions
+   *     relative to the cell hold an absolute precision of u a; a cluster of radius
+   *     0.05 a is resolved only to 20 u, which omega (growing like 1/radius) carries
+   *     past 1e-5.  Never seen in a fluid at N_c >= 1; crafted states only. */
+  ORC_FLAG_ILL_CONDITIONED = 4,
   ORC_FLAG_DEGENERATE = 8       /* n >= 3 but det(J) <= 0: omega set to zero */
 };
+
+#define ORC_COND_FLOAT32 20.0
+#define ORC_TIGHT_RMS 0.05
 
 /* observables slots (orc_step obs_out, 16 doubles) */
 enum {
@@ -76,6 +91,7 @@ void orc_srd_axis(const orc_params* p, int64_t step, uint32_t cell, double axis[
 void orc_rotate(const double axis[3], double alpha_rad, const double v[3], double out[3]);
 void orc_stream_one(const orc_params* p, uint32_t x[3], double v[3]);
 double orc_min_eigenvalue_sym3(const double A[9]);
+double orc_max_eigenvalue_sym3(const double A[9]);
 int orc_cell_omega(int64_t n, const double* rho, const double* w, double omega[3],
                    double rcm[3], double* sens);
 int orc_phantoms(const orc_params* p, int64_t step, uint32_t cell, double phi, int wall,

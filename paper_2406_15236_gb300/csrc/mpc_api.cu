@@ -456,8 +456,7 @@ size_t device_smem_limit(int device) {
 mpc_status plan_box(const mpc_params* p, size_t smem_limit, Geom& g, int64_t& N) {
   TRY(validate(p));
   g = Geom{};
-  int lmax = std::max(p->L[0], std::max(p->L[1], p->L[2]));
-  g.F = 31 - ceil_log2(lmax);
+  g.F = fixed_bits_for(p->L);
   g.mask = (1u << g.F) - 1u;
   for (int ax = 0; ax < 3; ++ax) {
     g.L[ax] = p->L[ax];
@@ -482,6 +481,7 @@ mpc_status plan_box(const mpc_params* p, size_t smem_limit, Geom& g, int64_t& N)
   g.n_c = p->n_c;
   g.key0 = (uint32_t)(p->seed & 0xffffffffu);
   g.key1 = (uint32_t)(p->seed >> 32);
+  round_keys(g);
   g.box = p->box_id;
   g.obs = (p->flags & MPC_FLAG_OBSERVABLES) ? 1 : 0;
   g.debug = (p->flags & MPC_FLAG_DEBUG_CELLS) ? 1 : 0;

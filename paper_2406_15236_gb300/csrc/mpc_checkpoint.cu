@@ -46,13 +46,6 @@ inline uint64_t cell_of(uint32_t x, uint32_t y, uint32_t z, int F, const int L[3
   return (uint64_t)(x >> F) + (uint64_t)L[0] * ((uint64_t)(y >> F) + (uint64_t)L[1] * (uint64_t)(z >> F));
 }
 
-int fixed_bits(const int L[3]) {
-  int lmax = std::max(L[0], std::max(L[1], L[2]));
-  int k = 0;
-  while ((1LL << k) < (long long)lmax) ++k;
-  return 31 - k;
-}
-
 mpc_status bad(const std::string& msg) { return fail(nullptr, MPC_EINVAL, "checkpoint: " + msg); }
 
 }  // namespace
@@ -181,7 +174,7 @@ mpc_status mpc_checkpoint_read(const char* prefix, void* stream, const mpc_alloc
     if (p.L[ax] < 2 || p.L[ax] > 1024) return bad("L out of range");
   if (N < 1 || N != std::llround((double)p.L[0] * p.L[1] * p.L[2] * p.n_c))
     return bad("n_particles does not match L and n_c");
-  if (F != fixed_bits(p.L)) return bad("fixed_bits does not match L");
+  if (F != mpc::fixed_bits_for(p.L)) return bad("fixed_bits does not match L");
   if (C != (uint64_t)p.L[0] * p.L[1] * p.L[2]) return bad("cells does not match L");
   if (off_bytes != (N >= (1LL << 32) ? 8 : 4)) return bad("offset_bytes does not match n_particles");
   if (step < 0) return bad("negative step");

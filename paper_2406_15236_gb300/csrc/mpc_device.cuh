@@ -23,28 +23,28 @@ enum : uint32_t {
 
 // Philox4x32-10 (Salmon et al., SC'11): per round, the two multiplier words give
 // 64-bit products whose high halves are mixed into the other pair of words with the
-// round key; the key advances by the Weyl increments after every round.
+// round key; the key advances by the Weyl increments after every round.  The ten round
+// keys depend on the seed alone, so the host computes them once (round_keys) and every
+// round xors a kernel-parameter word instead of adding the increments per draw.
 __device__ __forceinline__ uint4 philox4x32(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                            uint32_t k0, uint32_t k1) {
+                                            const uint32_t (&rk)[20]) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
     const uint32_t lo_a = 0xD2511F53u * c0;
     const uint32_t hi_a = __umulhi(0xD2511F53u, c0);
     const uint32_t lo_b = 0xCD9E8D57u * c2;
     const uint32_t hi_b = __umulhi(0xCD9E8D57u, c2);
-    c0 = hi_b ^ c1 ^ k0;
+    c0 = hi_b ^ c1 ^ rk[2 * r];
     c1 = lo_b;
-    c2 = hi_a ^ c3 ^ k1;
+    c2 = hi_a ^ c3 ^ rk[2 * r + 1];
     c3 = lo_a;
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
   }
   return make_uint4(c0, c1, c2, c3);
 }
 
 __device__ __forceinline__ uint4 draw(const Geom& g, uint32_t index, uint32_t step, uint32_t tag,
                                       uint32_t sub) {
-  return philox4x32(index, step, (tag << 24) | sub, g.box, g.key0, g.key1);
+  return philox4x32(index, step, (tag << 24) | sub, g.box, g.rk);
 }
 
 // (k + 1/2) 2^-23 from the top 23 bits: exact in float32

@@ -33,6 +33,7 @@ struct Geom {
   float kT, m;
   double n_c;        // mean density (phantom particles)
   uint32_t key0, key1, box;
+  uint32_t rk[20];   // Philox round keys: (key0 + r 0x9E3779B9, key1 + r 0xBB67AE85), r < 10
   int obs;           // accumulate observables
   int debug;         // keep collision cells and per-cell counts
   int det;           // fixed-point (order-independent) cell sums and observables
@@ -105,6 +106,24 @@ struct PackTable {
   StepArgs args[kPackGroup];
 };
 static_assert(sizeof(PackTable) <= 32000, "PackTable must fit in kernel parameter space");
+
+// Fixed-point fraction bits per cell of a box (the position contract): the largest
+// F with max(L) 2^F <= 2^31, so every position and its sum with a lattice shift fits in
+// 32 bits.  The one rule used by box planning, checkpoint files and the no-allocation sort.
+inline int fixed_bits_for(const int L[3]) {
+  const int lmax = L[0] > L[1] ? (L[0] > L[2] ? L[0] : L[2]) : (L[1] > L[2] ? L[1] : L[2]);
+  int k = 0;
+  while ((1LL << k) < (long long)lmax) ++k;
+  return 31 - k;
+}
+
+// Philox4x32-10 round keys of a seed (the key schedule of Salmon et al., SC'11)
+inline void round_keys(Geom& g) {
+  for (int r = 0; r < 10; ++r) {
+    g.rk[2 * r] = g.key0 + (uint32_t)r * 0x9E3779B9u;
+    g.rk[2 * r + 1] = g.key1 + (uint32_t)r * 0xBB67AE85u;
+  }
+}
 
 // launchers (mpc_step.cu)
 size_t step_smem_bytes(const Geom& g);

@@ -62,12 +62,6 @@ mpc_status scratch_for_current_device(uint32_t** out) {
   return MPC_OK;
 }
 
-int ceil_log2(int v) {
-  int k = 0;
-  while ((1LL << k) < (long long)v) ++k;
-  return k;
-}
-
 }  // namespace
 
 extern "C" mpc_status mpc_sort_by_cell_noalloc(const int32_t L[3], int64_t n, const uint32_t* X,
@@ -94,8 +88,7 @@ extern "C" mpc_status mpc_sort_by_cell_noalloc(const int32_t L[3], int64_t n, co
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
   Geom g{};
-  const int lmax = L[0] > L[1] ? (L[0] > L[2] ? L[0] : L[2]) : (L[1] > L[2] ? L[1] : L[2]);
-  g.F = 31 - ceil_log2(lmax);
+  g.F = fixed_bits_for(L);
   g.mask = (1u << g.F) - 1u;
   for (int ax = 0; ax < 3; ++ax) {
     g.L[ax] = L[ax];

@@ -315,7 +315,41 @@ struct BrickShared {
   uint32_t cnt, halt;
   int64_t step;
   uint32_t gcount[28], gbase[28], gdest[28];
+  uint32_t shift[6];  // lattice shifts of this step and the next
 };
+
+// omega = J^-1 L for the moments M = sum r r^T and L = sum r x w about a cell's centre of
+// mass (J = tr(M) 1 - M): the adjugate for n >= 3 (zero when det J <= 0, a collinear
+// cell), the pseudo-inverse on the plane normal to the pair for n = 2, zero for n < 2
+__device__ __forceinline__ float3 solve_omega(int n, float Mxx, float Myy, float Mzz, float Mxy,
+                                              float Myz, float Mzx, float Lx, float Ly, float Lz) {
+  const float tr = Mxx + Myy + Mzz;
+  float3 om = make_float3(0.0f, 0.0f, 0.0f);
+  if (n >= 3) {
+    const float Jxx = tr - Mxx, Jyy = tr - Myy, Jzz = tr - Mzz;
+    const float Jxy = -Mxy, Jyz = -Myz, Jzx = -Mzx;
+    const float A00 = Jyy * Jzz - Jyz * Jyz, A01 = Jzx * Jyz - Jxy * Jzz,
+                A02 = Jxy * Jyz - Jzx * Jyy, A11 = Jxx * Jzz - Jzx * Jzx,
+                A12 = Jzx * Jxy - Jxx * Jyz, A22 = Jxx * Jyy - Jxy * Jxy;
+    const float det = Jxx * A00 + Jxy * A01 + Jzx * A02;
+    if (det > 0.0f) {
+      const float id = 1.0f / det;
+      om.x = (A00 * Lx + A01 * Ly + A02 * Lz) * id;
+      om.y = (A01 * Lx + A11 * Ly + A12 * Lz) * id;
+      om.z = (A02 * Lx + A12 * Ly + A22 * Lz) * id;
+    }
+  } else if (n == 2 && tr > 0.0f) {
+    // pair: J = tr(M) (1 - d d^T/|d|^2); pseudo-inverse on the plane normal to d
+    const float it = 1.0f / tr;
+    const float mLx = (Mxx * Lx + Mxy * Ly + Mzx * Lz) * it;
+    const float mLy = (Mxy * Lx + Myy * Ly + Myz * Lz) * it;
+    const float mLz = (Mzx * Lx + Myz * Ly + Mzz * Lz) * it;
+    om.x = (Lx - mLx) * it;
+    om.y = (Ly - mLy) * it;
+    om.z = (Lz - mLz) * it;
+  }
+  return om;
+}
 
 // --- one brick of one box ---------------------------------------------------------
 // Processes brick b of the box described by `a`.  PERSIST: the caller initialised
@@ -411,16 +445,13 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
   const PBuf& dst = a.buf[par ^ 1];
   uint32_t* cnt_dst = a.cnt[par ^ 1];
   const int cnt = (int)sh.cnt;
-  // lattice shifts of this step and the next: one lane per warp draws, the warp shares
-  uint3 s0 = make_uint3(0, 0, 0), s1 = make_uint3(0, 0, 0);
-  if (lane == 0) {
-    s0 = lattice_shift(g, step);
-    s1 = lattice_shift(g, step + 1);
+  // lattice shifts of this step and the next, drawn by one thread each while the bulk
+  // copies are in flight; the barrier after the wait publishes them
+  if (tid == 0 || tid == 32) {
+    const uint3 t = lattice_shift(g, step + (tid >> 5));
+    uint32_t* o = sh.shift + 3 * (tid >> 5);
+    o[0] = t.x; o[1] = t.y; o[2] = t.z;
   }
-  const uint32_t S0x = __shfl_sync(0xffffffffu, s0.x, 0), S0y = __shfl_sync(0xffffffffu, s0.y, 0),
-                 S0z = __shfl_sync(0xffffffffu, s0.z, 0);
-  const uint32_t S1x = __shfl_sync(0xffffffffu, s1.x, 0), S1y = __shfl_sync(0xffffffffu, s1.y, 0),
-                 S1z = __shfl_sync(0xffffffffu, s1.z, 0);
   {
     // every thread waits (bounded); the block leaves together if any wait gave up
     const bool ok = mbar_wait(&sh.bar, phase);
@@ -431,6 +462,8 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
     }
     phase ^= 1u;
   }
+  const uint32_t S0x = sh.shift[0], S0y = sh.shift[1], S0z = sh.shift[2];
+  const uint32_t S1x = sh.shift[3], S1y = sh.shift[4], S1z = sh.shift[5];
 
   const int bx = b % g.nb[0];
   const int by = (b / g.nb[0]) % g.nb[1];
@@ -626,7 +659,6 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
         // w (AT+a: w = v - v_ran; SRD+a: w = v, so the mean is v_cm)
         float r0 = 0.f, r1 = 0.f, r2 = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f;
         constexpr bool kOnePass = VAR == 1 && !DET;
-        constexpr int kOnePassMin = 6;
         float o_m[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if constexpr (DET) {
           // positions sum exactly as integers; velocities in fixed point
@@ -668,10 +700,23 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
         const float inv = 1.0f / fmaxf((float)n, 1.0f);
         const float rcx = r0 * inv, rcy = r1 * inv, rcz = r2 * inv;
         const float wmx = w0 * inv, wmy = w1 * inv, wmz = w2 * inv;
-        // cells of kOnePassMin or more members take their moments from the raw sums;
-        // the smaller ones (where a near-degenerate configuration is likelier) take the
-        // second pass
-        const bool second = !kOnePass || n < kOnePassMin;
+        // float AT+a takes the moments from the first pass's raw sums about the cell
+        // centre, M = sum rho rho^T - n rho_c rho_c^T and L = sum rho x w - n rho_c x <w>;
+        // where the members sit close together away from the centre these differences
+        // cancel (sum |rho|^2 > 4 tr M), and such cells take the second pass about the
+        // centre of mass
+        float Mxx = 0.f, Myy = 0.f, Mzz = 0.f, Mxy = 0.f, Myz = 0.f, Mzx = 0.f;
+        float Lx = 0.f, Ly = 0.f, Lz = 0.f;
+        bool second = true;
+        if constexpr (kOnePass) {
+          const float fn = (float)n;
+          Mxx = o_m[0] - fn * rcx * rcx; Myy = o_m[1] - fn * rcy * rcy; Mzz = o_m[2] - fn * rcz * rcz;
+          Mxy = o_m[3] - fn * rcx * rcy; Myz = o_m[4] - fn * rcy * rcz; Mzx = o_m[5] - fn * rcz * rcx;
+          Lx = o_m[6] - fn * (rcy * wmz - rcz * wmy);
+          Ly = o_m[7] - fn * (rcz * wmx - rcx * wmz);
+          Lz = o_m[8] - fn * (rcx * wmy - rcy * wmx);
+          second = n >= 2 && o_m[0] + o_m[1] + o_m[2] > 4.0f * (Mxx + Myy + Mzz);
+        }
         // SRD+a: the cell's random rotation axis (every lane of the group draws it)
         float ax = 0.f, ay = 0.f, az = 0.f;
         if constexpr (VAR == 2) {
@@ -685,8 +730,8 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
         }
         // second pass: moments about the centre of mass and the angular momentum the
         // collision would change -- AT+a: of w - <w>; SRD+a (Eq. 4): of v_ic - D v_ic
-        float Mxx = 0.f, Myy = 0.f, Mzz = 0.f, Mxy = 0.f, Myz = 0.f, Mzx = 0.f;
-        float Lx = 0.f, Ly = 0.f, Lz = 0.f;
+        float sMxx = 0.f, sMyy = 0.f, sMzz = 0.f, sMxy = 0.f, sMyz = 0.f, sMzx = 0.f;
+        float sLx = 0.f, sLy = 0.f, sLz = 0.f;
         long long qM[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // deterministic mode
         const bool any_second = !kOnePass || __any_sync(0xffffffffu, second && n > 0);
         const int n2 = second ? n : 0;
@@ -710,9 +755,9 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
             qM[3] += to_fx(rx * ry); qM[4] += to_fx(ry * rz); qM[5] += to_fx(rz * rx);
             qM[6] += to_fx(tx); qM[7] += to_fx(ty); qM[8] += to_fx(tz);
           } else {
-            Mxx += rx * rx; Myy += ry * ry; Mzz += rz * rz;
-            Mxy += rx * ry; Myz += ry * rz; Mzx += rz * rx;
-            Lx += ry * wz - rz * wy; Ly += rz * wx - rx * wz; Lz += rx * wy - ry * wx;
+            sMxx += rx * rx; sMyy += ry * ry; sMzz += rz * rz;
+            sMxy += rx * ry; sMyz += ry * rz; sMzx += rz * rx;
+            sLx += ry * wz - rz * wy; sLy += rz * wx - rx * wz; sLz += rx * wy - ry * wx;
           }
         }
         if constexpr (DET) {
@@ -723,46 +768,19 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
           Lx = from_fx(qM[6]); Ly = from_fx(qM[7]); Lz = from_fx(qM[8]);
         } else {
           if (any_second) {
-            Mxx = group_sum(Mxx, tpc); Myy = group_sum(Myy, tpc); Mzz = group_sum(Mzz, tpc);
-            Mxy = group_sum(Mxy, tpc); Myz = group_sum(Myz, tpc); Mzx = group_sum(Mzx, tpc);
-            Lx = group_sum(Lx, tpc); Ly = group_sum(Ly, tpc); Lz = group_sum(Lz, tpc);
+            sMxx = group_sum(sMxx, tpc); sMyy = group_sum(sMyy, tpc); sMzz = group_sum(sMzz, tpc);
+            sMxy = group_sum(sMxy, tpc); sMyz = group_sum(sMyz, tpc); sMzx = group_sum(sMzx, tpc);
+            sLx = group_sum(sLx, tpc); sLy = group_sum(sLy, tpc); sLz = group_sum(sLz, tpc);
           }
-          if (!second) {
-            const float fn = (float)n;
-            Mxx = o_m[0] - fn * rcx * rcx; Myy = o_m[1] - fn * rcy * rcy; Mzz = o_m[2] - fn * rcz * rcz;
-            Mxy = o_m[3] - fn * rcx * rcy; Myz = o_m[4] - fn * rcy * rcz; Mzx = o_m[5] - fn * rcz * rcx;
-            Lx = o_m[6] - fn * (rcy * wmz - rcz * wmy);
-            Ly = o_m[7] - fn * (rcz * wmx - rcx * wmz);
-            Lz = o_m[8] - fn * (rcx * wmy - rcy * wmx);
+          if (second) {
+            Mxx = sMxx; Myy = sMyy; Mzz = sMzz; Mxy = sMxy; Myz = sMyz; Mzx = sMzx;
+            Lx = sLx; Ly = sLy; Lz = sLz;
           }
         }
         if (exists && n > 0 && sub == 0) {
-          const float tr = Mxx + Myy + Mzz;
-          float ox_ = 0.0f, oy_ = 0.0f, oz_ = 0.0f;
-          if (n >= 3) {
-            // J = tr(M) 1 - M (moment-of-inertia tensor per unit mass); omega = J^-1 L
-            const float Jxx = tr - Mxx, Jyy = tr - Myy, Jzz = tr - Mzz;
-            const float Jxy = -Mxy, Jyz = -Myz, Jzx = -Mzx;
-            const float A00 = Jyy * Jzz - Jyz * Jyz, A01 = Jzx * Jyz - Jxy * Jzz,
-                        A02 = Jxy * Jyz - Jzx * Jyy, A11 = Jxx * Jzz - Jzx * Jzx,
-                        A12 = Jzx * Jxy - Jxx * Jyz, A22 = Jxx * Jyy - Jxy * Jxy;
-            const float det = Jxx * A00 + Jxy * A01 + Jzx * A02;
-            if (det > 0.0f) {
-              const float id = 1.0f / det;
-              ox_ = (A00 * Lx + A01 * Ly + A02 * Lz) * id;
-              oy_ = (A01 * Lx + A11 * Ly + A12 * Lz) * id;
-              oz_ = (A02 * Lx + A12 * Ly + A22 * Lz) * id;
-            }
-          } else if (n == 2 && tr > 0.0f) {
-            // pair: J = tr(M) (1 - d d^T/|d|^2); pseudo-inverse on the plane normal to d
-            const float it = 1.0f / tr;
-            const float mLx = (Mxx * Lx + Mxy * Ly + Mzx * Lz) * it;
-            const float mLy = (Mxy * Lx + Myy * Ly + Myz * Lz) * it;
-            const float mLz = (Mzx * Lx + Myz * Ly + Mzz * Lz) * it;
-            ox_ = (Lx - mLx) * it;
-            oy_ = (Ly - mLy) * it;
-            oz_ = (Lz - mLz) * it;
-          }
+          // J = tr(M) 1 - M (moment-of-inertia tensor per unit mass); omega = J^-1 L
+          const float3 om = solve_omega(n, Mxx, Myy, Mzz, Mxy, Myz, Mzx, Lx, Ly, Lz);
+          const float ox_ = om.x, oy_ = om.y, oz_ = om.z;
           float* P = spar + lc;
           P[0 * bc] = wmx; P[1 * bc] = wmy; P[2 * bc] = wmz;
           P[3 * bc] = ox_; P[4 * bc] = oy_; P[5 * bc] = oz_;

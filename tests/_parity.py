@@ -1,21 +1,28 @@
 """Helpers for GPU-vs-oracle parity tests (test infrastructure).
 
-Velocity error of a particle: |v_gpu - v_ref| / max(|v_ref|, sqrt(kT/m)), bar 1e-5.
-For the angular-momentum variants the float32 kernel solves J omega = L per cell, and
-float32 rounding (relative u = 2^-24 per operation) of the products and of the
-centre-of-mass positions reaches the velocity amplified by the first-order factor sens_i
-the oracle exports (1/lambda_min(J) times the perturbations of L and J, times |r_i|,
-plus the rounding of r_i times |omega|); the bar of a particle is
-max(1e-5, 16 u sens_i / scale_i).  It widens only for near-collinear cells and
-near-coincident pairs of 2-5 particles.
-Integer results (positions, collision cells, per-cell counts) must agree bit-exactly.
+Velocity error of a particle: |v_gpu - v_ref| / max(|v_ref|, sqrt(kT/m)), bar 1e-5 for
+every particle of every cell, except:
+  * cells the oracle flags FLAG_ILL_CONDITIONED (angular-momentum variants, n >= 3,
+    cond(J) > 20, about 0.2 % of the cells at N_c = 10): a float32 solve is good there
+    only to the first-order sensitivity sens_i the oracle exports (pinned against
+    float32 evaluations by tests/test_oracle_sensitivity.py: errors up to 0.44 u sens_i;
+    the kernel's measured up to 0.7 u sens_i), so their members' bar is
+    max(1e-5, 4 u sens_i / scale_i), u = 2^-24;
+  * cells with a flag in `strict_flags` (a float32 sampler decision within 1e-5 of its
+    threshold, or a degenerate inertia tensor), which are not compared.
+check_step reports the share of ill-conditioned cells per step.  Integer results
+(positions, collision cells, per-cell counts) must agree bit-exactly.
 """
+import json
+import os
+
 import numpy as np
 
 import oracle
 
 VEL_TOL = 1e-5
 ULP32 = 2.0**-24
+SENS_FACTOR = 4  # bar in an ill-conditioned cell: max(1e-5, SENS_FACTOR u sens_i / scale_i)
 
 
 def by_id(X, V, ids, cell=None):
@@ -33,6 +40,28 @@ def oracle_params(**kw):
               "obs_ring"):
         m.pop(k, None)
     return oracle.params(variant=variant, g=g, **m)
+
+
+def cell_condition(p_oracle, X_streamed, step, cell, ncells):
+    """cond(J) per collision cell (inf for cells of fewer than three members or a
+    degenerate J): J = tr(M) 1 - M, M = sum r r^T about the cell's centre of mass, from the
+    oracle's collision positions"""
+    F = oracle.fixed_bits(p_oracle)
+    S = oracle.shift(p_oracle, step).astype(np.int64)
+    rho = (((X_streamed.astype(np.int64) + S[:, None]) & ((1 << F) - 1)) / 2.0**F - 0.5).T
+    n = np.bincount(cell, minlength=ncells).astype(np.float64)
+    s1 = np.zeros((ncells, 3))
+    s2 = np.zeros((ncells, 3, 3))
+    np.add.at(s1, cell, rho)
+    np.add.at(s2, cell, rho[:, :, None] * rho[:, None, :])
+    nn = np.maximum(n, 1.0)[:, None, None]
+    M = s2 - s1[:, :, None] * s1[:, None, :] / nn
+    J = np.trace(M, axis1=1, axis2=2)[:, None, None] * np.eye(3) - M
+    ev = np.linalg.eigvalsh(J)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        cond = np.where(ev[:, 0] > 0, ev[:, 2] / ev[:, 0], np.inf)
+    cond[n < 3] = np.inf
+    return cond, n
 
 
 def check_step(p_oracle, pre, post, step, kT=1.0, m=1.0, post_cells=None, gpu_counts=None,
@@ -61,14 +90,47 @@ def check_step(p_oracle, pre, post, step, kT=1.0, m=1.0, post_cells=None, gpu_co
     scale = np.maximum(np.linalg.norm(vref, axis=0), np.sqrt(kT / m))
     err = np.linalg.norm(V1.astype(np.float64) - vref, axis=0) / scale
     flagged = (ref["flags"][ref["cell"]] & strict_flags) != 0
-    bar = np.maximum(VEL_TOL, 16 * ULP32 * ref["sens"] / scale)
+    illc = (ref["flags"][ref["cell"]] & oracle.FLAG_ILL_CONDITIONED) != 0
+    bar = np.where(illc, np.maximum(VEL_TOL, SENS_FACTOR * ULP32 * ref["sens"] / scale), VEL_TOL)
     ratio = err / bar
+    with np.errstate(divide="ignore", invalid="ignore"):
+        k_emp = np.where(ref["sens"] > 0, err * scale / (ULP32 * ref["sens"]), 0.0)
+    stats["k_emp"] = float(k_emp.max())  # largest error in units of u sens_i
+    stats["k_emp_ill"] = float(k_emp[illc].max()) if illc.any() else 0.0
+    occupied = max(1, int((ref["counts"] > 0).sum()))
+    stats["ill_cells"] = float(((ref["flags"] & oracle.FLAG_ILL_CONDITIONED) != 0).sum() / occupied)
+    stats["ill_particles"] = float(illc.mean())
+    strict = ~flagged & ~illc
+    stats["over_tol_strict"] = float((err[strict] > VEL_TOL).mean()) if strict.any() else 0.0
+    stats["max_err_strict"] = float(err[strict].max()) if strict.any() else 0.0
     stats["max_err"] = float(err[~flagged].max()) if (~flagged).any() else 0.0
     stats["max_ratio"] = float(ratio[~flagged].max()) if (~flagged).any() else 0.0
     stats["widened"] = float((bar[~flagged] > VEL_TOL).mean()) if (~flagged).any() else 0.0
     stats["over_tol"] = float((err[~flagged] > VEL_TOL).mean()) if (~flagged).any() else 0.0
     stats["flagged"] = int(flagged.sum())
     stats["max_err_flagged"] = float(err[flagged].max()) if flagged.any() else 0.0
+    log_path = os.environ.get("MPC_PARITY_LOG")
+    if log_path and ref["sens"].max() > 0:  # angular-momentum variants: conditioning report
+        cond, n = cell_condition(p_oracle, ref["X"], step, ref["cell"], len(ref["flags"]))
+        pc = cond[ref["cell"]]
+        over = err > VEL_TOL
+        stats["cond_over_tol_min"] = float(pc[over].min()) if over.any() else None
+        stats["n_over_tol"] = int(over.sum())
+        stats["n_over_tol_pairs"] = int((over & (n[ref["cell"]] == 2)).sum())
+        occupied = n > 0
+        for t in (10, 30, 100, 300, 1000):
+            stats[f"cells_cond_gt_{t}"] = float(((cond > t) & (n >= 3)).sum() / occupied.sum())
+        stats["cells_pairs"] = float((n == 2).sum() / occupied.sum())
+        for t in (10, 30, 100):
+            ok = pc <= t
+            stats[f"max_err_cond_le_{t}"] = float(err[ok].max()) if ok.any() else 0.0
+    if log_path:  # one line per checked step, for reports
+        with open(log_path, "a") as f:
+            f.write(json.dumps({"test": os.environ.get("PYTEST_CURRENT_TEST", ""), "step": step,
+                                **{k: v for k, v in stats.items()}}) + "\n")
+    assert stats["over_tol_strict"] == 0.0, (f"step {step}: velocity error "
+                                             f"{stats['max_err_strict']:.3g} above 1e-5 in a cell "
+                                             f"that is not ill-conditioned")
     assert stats["max_ratio"] <= 1.0, (f"step {step}: velocity error {stats['max_err']:.3g} "
                                        f"exceeds its bar (ratio {stats['max_ratio']:.3g})")
     stats["ref"] = ref

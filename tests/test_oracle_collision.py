@@ -185,5 +185,51 @@ def test_min_eigenvalue_matches_numpy():
         A = A @ A.T * rng.uniform(1e-4, 10)
         if rng.random() < 0.2:
             A = np.diag(np.diag(A))
-        ref = np.linalg.eigvalsh(A)[0]
-        assert abs(oracle.min_eigenvalue_sym3(A) - ref) <= 1e-9 * np.abs(A).max()
+        ref = np.linalg.eigvalsh(A)
+        assert abs(oracle.min_eigenvalue_sym3(A) - ref[0]) <= 1e-9 * np.abs(A).max()
+        assert abs(oracle.max_eigenvalue_sym3(A) - ref[2]) <= 1e-9 * np.abs(A).max()
+
+
+def test_ill_conditioned_flag_follows_the_eigenvalue_ratio():
+    """FLAG_ILL_CONDITIONED marks the cells of three or more members whose inertia tensor
+    has lambda_max / lambda_min above COND_FLOAT32 (checked with numpy's eigvalsh on the
+    oracle's own collision positions), and no others."""
+    p = oracle.params(L=12, n_c=4.0, h=0.05, variant=oracle.AT_A, seed=21)
+    X, V, ids = oracle.init(p)
+    r = oracle.step(p, X, V, ids, 0, cells=True, counts=True, flags=True)
+    F = oracle.fixed_bits(p)
+    S = oracle.shift(p, 0).astype(np.int64)
+    rho = (((r["X"].astype(np.int64) + S[:, None]) & ((1 << F) - 1)) / 2.0**F - 0.5).T
+    flagged, checked = 0, 0
+    for c in np.flatnonzero(r["counts"] >= 3):
+        m = rho[r["cell"] == c]
+        q = m - m.mean(axis=0)
+        J = (q * q).sum() * np.eye(3) - q.T @ q
+        ev = np.linalg.eigvalsh(J)
+        ill = ev[2] > oracle.COND_FLOAT32 * ev[0]
+        if abs(ev[2] / ev[0] / oracle.COND_FLOAT32 - 1.0) < 1e-9:
+            continue  # on the threshold
+        assert bool(r["flags"][c] & oracle.FLAG_ILL_CONDITIONED) == ill, c
+        flagged += ill
+        checked += 1
+    assert checked > 1000 and flagged > 10  # N_c = 4: small cells, often ill-conditioned
+
+
+def test_tight_clusters_are_flagged():
+    """Members within TIGHT_RMS (rms) of their centre of mass are flagged
+    FLAG_ILL_CONDITIONED whatever the shape; slightly wider clusters of the same shape
+    are not."""
+    rng = np.random.default_rng(4)
+    for n in (2, 3, 6):
+        for _ in range(20):
+            shape = rng.normal(size=(n, 3))
+            shape -= shape.mean(axis=0)
+            shape /= np.sqrt((shape**2).sum() / n)  # rms radius 1
+            c = rng.uniform(-0.3, 0.3, 3)
+            w = rng.normal(size=(n, 3))
+            ev = np.linalg.eigvalsh((shape**2).sum() * np.eye(3) - shape.T @ shape)
+            if n >= 3 and ev[2] > 0.5 * oracle.COND_FLOAT32 * ev[0]:
+                continue  # keep clear of the conditioning criterion
+            for rms, expect in ((0.9 * oracle.TIGHT_RMS, True), (1.1 * oracle.TIGHT_RMS, False)):
+                _, _, _, fl = oracle.cell_omega(c + rms * shape, w)
+                assert bool(fl & oracle.FLAG_ILL_CONDITIONED) == expect, (n, rms)
