@@ -244,6 +244,38 @@ def cpu_oracle_rate(args, budget: float, warm: int = 0, max_steps: int = 10**9, 
     return total / wall, cores, sample
 
 
+def cpu_single_core_rates(args, steps=(("16", 10), ("64", 10), ("128", 3))):
+    """The single-threaded oracle on config 1 (L = 16) and on L = 64 and 128, SRD and AT+a,
+    each in its own process (the six run side by side on separate host cores); per-core
+    particle-steps/s, and the L = 512 rates extrapolated from L = 128 (per-particle cost
+    taken as constant; the 64 GB FP64 state of L = 512 is not run)."""
+    import multiprocessing as mp
+
+    import oracle
+
+    oracle.build()
+    jobs, names = [], []
+    for L, n in steps:
+        for variant, h, tag in ((0, 0.1, "srd"), (1, 0.05, "at_a")):
+            jobs.append((int(L), args.n_c, variant, h, 7, 0, 1e9, n))
+            names.append(f"L{L}_{tag}")
+    with mp.get_context("spawn").Pool(min(len(jobs), os.cpu_count() or 1)) as pool:
+        res = pool.map(_oracle_worker, jobs)
+    rates = {nm: n_p * n / t for nm, (n_p, n, t) in zip(names, res)}
+    out = {"unit": UNIT + " per core",
+           "sample": "oracle (single-threaded C, FP64), one process per case, six side by side; "
+                     + ", ".join(f"L={L}: {n} steps" for L, n in steps)
+                     + f"; N_c={args.n_c:g}; SRD h=0.1, AT+a h=0.05",
+           "rates": rates}
+    n512 = 512**3 * args.n_c
+    out["extrapolated_L512"] = {
+        "note": "extrapolated from L=128 (per-particle cost taken as constant); not run",
+        "srd_seconds_per_step_one_core": n512 / rates["L128_srd"],
+        "at_a_seconds_per_step_one_core": n512 / rates["L128_at_a"],
+        "srd_rate_one_core": rates["L128_srd"], "at_a_rate_one_core": rates["L128_at_a"]}
+    return out
+
+
 # --- reference arm ---------------------------------------------------------------------------------
 
 def run_reference(args):
@@ -570,8 +602,15 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
+        single = cpu_single_core_rates(args)
         rate, cores, sample = cpu_oracle_rate(args, budget=args.cpu_seconds, L=32)
-        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+               "single_core": single}
+        key = "at_a" if args.variant == "at_a" else "srd"
+        cpu["extrapolated_L512_all_cores"] = {
+            "note": "extrapolated: the L=128 single-core rate times the all-core speed-up "
+                    "measured at L=32 over the single-core L=64 rate; not run",
+            "rate": single["rates"][f"L128_{key}"] * rate / single["rates"][f"L64_{key}"]}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

@@ -181,6 +181,14 @@ mpc_status mpc_observables(mpc_handle h, mpc_obs* out);
  * number of rows written in *written.  Synchronises. */
 mpc_status mpc_observable_series(mpc_handle h, double* rows, int64_t count, int64_t* written);
 
+/* Velocity profile across the box along z (Sec. II, "External fields" and "Boundary
+ * conditions": the flow between walls under a body force): the box [0, L_z) is cut into
+ * nbins equal slabs; out (host, 4 nbins doubles) receives per slab the number of
+ * particles and the sums of v_x, v_y and v_z over them, at the positions and velocities
+ * of the current state (those mpc_get_state returns).  nbins in [1, 65536], else
+ * MPC_EINVAL.  Allocates a 32 nbins-byte device buffer for the call.  Synchronises. */
+mpc_status mpc_velocity_profile(mpc_handle h, int32_t nbins, double* out);
+
 mpc_status mpc_get_info(mpc_handle h, mpc_info* out);
 
 /* Timing support (no counterpart in the paper beyond its per-partial-step timers,

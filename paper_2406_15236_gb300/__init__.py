@@ -148,6 +148,7 @@ def lib():
     L.mpc_get_cell_counts.argtypes = [vp, vp, ctypes.c_int]
     L.mpc_observables.argtypes = [vp, P(mpc_obs)]
     L.mpc_observable_series.argtypes = [vp, vp, ctypes.c_int64, P(ctypes.c_int64)]
+    L.mpc_velocity_profile.argtypes = [vp, ctypes.c_int32, vp]
     L.mpc_get_info.argtypes = [vp, P(mpc_info)]
     L.mpc_set_profiling.argtypes = [vp, ctypes.c_int]
     L.mpc_profile_step_kernel.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_int32)]
@@ -183,7 +184,8 @@ def lib():
     L.mpc_version.restype = ctypes.c_char_p
     for name in ("mpc_create", "mpc_destroy", "mpc_step", "mpc_synchronize", "mpc_get_state",
                  "mpc_set_state", "mpc_get_cell_counts", "mpc_observables",
-                 "mpc_observable_series", "mpc_get_info", "mpc_set_profiling",
+                 "mpc_observable_series", "mpc_velocity_profile", "mpc_get_info",
+                 "mpc_set_profiling",
                  "mpc_profile_step_kernel", "mpc_sort_by_cell_noalloc", "mpc_set_step_limit",
                  "mpc_checkpoint_write", "mpc_checkpoint_read",
                  "mpc_footprint", "mpc_autotune", "mpc_batch_create", "mpc_batch_destroy",
@@ -325,6 +327,12 @@ def mpc_observable_series(handle, rows: np.ndarray) -> int:
     _check(lib().mpc_observable_series(handle, rows.ctypes.data, rows.shape[0], ctypes.byref(n)),
            handle)
     return n.value
+
+
+def mpc_velocity_profile(handle, out: np.ndarray) -> None:
+    """out: float64 (nbins, 4) host array: per z slab count, sum vx, sum vy, sum vz"""
+    assert out.dtype == np.float64 and out.ndim == 2 and out.shape[1] == 4 and out.flags.c_contiguous
+    _check(lib().mpc_velocity_profile(handle, out.shape[0], out.ctypes.data), handle)
 
 
 def mpc_get_info(handle) -> mpc_info:
@@ -531,6 +539,12 @@ class Box:
         rows = np.zeros((count, 16), dtype=np.float64)
         n = mpc_observable_series(self.handle, rows)
         return rows[:n]
+
+    def velocity_profile(self, nbins: int):
+        """(counts (nbins,), summed velocities (nbins, 3)) per z slab of the box"""
+        out = np.zeros((nbins, 4), dtype=np.float64)
+        mpc_velocity_profile(self.handle, out)
+        return out[:, 0], out[:, 1:]
 
 
 class Simulation(Box):

@@ -792,6 +792,25 @@ mpc_status mpc_get_cell_counts(mpc_handle h, uint32_t* counts, int device_ptrs) 
   return MPC_OK;
 }
 
+mpc_status mpc_velocity_profile(mpc_handle h, int32_t nbins, double* out) {
+  if (!h) return fail(nullptr, MPC_EINVAL, "handle is NULL");
+  if (!out) return fail(h, MPC_EINVAL, "out is NULL");
+  if (nbins < 1 || nbins > 65536) return fail(h, MPC_EINVAL, "nbins must lie in [1, 65536]");
+  TRY(set_device(h));
+  TRY(sync_and_repair(h));
+  double* part = nullptr;
+  TRY(alloc_array(h, &part, (size_t)nbins * 4, "velocity profile"));
+  const int par = (int)(h->ctrl_host->step & 1);
+  cudaError_t e = cudaMemsetAsync(part, 0, sizeof(double) * 4 * (size_t)nbins, h->stream);
+  if (e == cudaSuccess) e = launch_velocity_profile(h->g, h->buf[par], h->cnt[par], nbins, part, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, part, sizeof(double) * 4 * (size_t)nbins, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  dev_free(h, part);
+  if (e != cudaSuccess) return fail(h, MPC_ECUDA, std::string("velocity profile: ") + cudaGetErrorString(e));
+  return MPC_OK;
+}
+
 mpc_status mpc_observables(mpc_handle h, mpc_obs* out) {
   if (!h) return fail(nullptr, MPC_EINVAL, "handle is NULL");
   if (!out) return fail(h, MPC_EINVAL, "out is NULL");

@@ -169,5 +169,8 @@ cudaError_t launch_cell_scatter(const Geom& g, int64_t N, const PBuf& src, uint3
                                 const PBuf& dst, cudaStream_t s);
 cudaError_t launch_reduce_obs(const Geom& g, const PBuf& b, const uint32_t* cnt, double* out,
                               cudaStream_t s);
+// per slab of nbins along z: count, sum vx, sum vy, sum vz (out: 4 nbins doubles, zeroed)
+cudaError_t launch_velocity_profile(const Geom& g, const PBuf& b, const uint32_t* cnt, int nbins,
+                                    double* out, cudaStream_t s);
 
 }  // namespace mpc

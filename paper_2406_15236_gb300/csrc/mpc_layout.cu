@@ -288,7 +288,34 @@ __global__ void k_reduce_obs(const Geom g, PBuf b, const uint32_t* cnt, double* 
   }
 }
 
+// Velocity profile across the box along z: nbins equal slabs of [0, L_z); per slab the
+// particle count and the sums of the velocity components, at the positions of the state
+// contract (the stored, streamed positions unstreamed).  Global double atomics: an
+// analysis pass, not part of the step.
+__global__ void k_velocity_profile(const Geom g, PBuf b, const uint32_t* cnt, int nbins, double* out) {
+  const int br = blockIdx.x;
+  const uint32_t c = min(cnt[br], (uint32_t)g.cap);
+  const size_t o = (size_t)br * g.cap;
+  for (uint32_t k = threadIdx.x; k < c; k += blockDim.x) {
+    uint32_t x = b.x[0][o + k], y = b.x[1][o + k], z = b.x[2][o + k];
+    const float vx = b.v[0][o + k], vy = b.v[1][o + k], vz = b.v[2][o + k];
+    unstream(g, x, y, z, vx, vy, vz);
+    const uint64_t slab = ((uint64_t)z * (uint64_t)nbins) / (uint64_t)g.P[2];
+    double* q = out + 4 * min((int)slab, nbins - 1);
+    atomicAdd(q, 1.0);
+    atomicAdd(q + 1, (double)vx);
+    atomicAdd(q + 2, (double)vy);
+    atomicAdd(q + 3, (double)vz);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_velocity_profile(const Geom& g, const PBuf& b, const uint32_t* cnt, int nbins,
+                                    double* out, cudaStream_t s) {
+  k_velocity_profile<<<g.nbricks, kBlock, 0, s>>>(g, b, cnt, nbins, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_init_particles(const Geom& g, int64_t N, uint32_t* const x[3], float* const v[3],
                                   uint32_t* id, double* sums, cudaStream_t s) {

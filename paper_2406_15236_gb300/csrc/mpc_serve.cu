@@ -80,8 +80,9 @@ mpc_status sfail(mpc_server s, mpc_status st, const std::string& msg) {
 // Green-Kubo shear viscosity from per-step stress rows (Sec. II observables; the MPC
 // stress of the streaming and collision parts): eta = (V h / kT) [C(0)/2 + sum_{k=1..K}
 // C(k)], C the autocorrelation of each off-diagonal stress about its mean, averaged
-// over xy, yx, yz, zy, zx, xz; K = clamp(steps / 10, 10, 50): the MPC stress
-// decorrelates within a few steps, and longer windows only add noise.
+// over xy, yx, yz, zy, zx, xz; K = one time unit of steps, round(1 / h): the MPC stress
+// autocorrelation has decayed by then (windows of half, one and two time units give the
+// same viscosity within the noise), and longer windows only add noise.
 void green_kubo(const mpc_params& p, int64_t N, const double* rows, int64_t n, double& eta,
                 double& temp) {
   const double vol = (double)p.L[0] * p.L[1] * p.L[2];
@@ -96,7 +97,7 @@ void green_kubo(const mpc_params& p, int64_t N, const double* rows, int64_t n, d
   temp = n > 0 ? temp / (double)n : 0.0;
   eta = 0.0;
   if (n < 4) return;
-  const int64_t K = std::min<int64_t>(std::max<int64_t>(n / 10, 10), std::min<int64_t>(50, n - 1));
+  const int64_t K = std::min<int64_t>(std::max<int64_t>(std::llround(1.0 / p.h), 1), n - 1);
   std::vector<double> sig((size_t)n);
   double acc = 0.0;
   for (int c = 0; c < 6; ++c) {

@@ -1,0 +1,116 @@
+"""Plane Poiseuille flow on the GPU (Sec. II: "External fields", "Boundary conditions",
+"Thermostat", Eqs. 5-7): SRD (alpha 130 deg, h 0.1, N_c 10) with the cell-level
+Maxwell-Boltzmann-scaling thermostat, no-slip walls at z = 0 and z = L_z (bounce-back and
+phantom particles), a body force g along x, the fluid at rest at t = 0.
+
+Closed form of the incompressible start-up flow between no-slip walls (rho = N_c m,
+nu = eta / rho):
+    v_x(z, t) = (rho g / 2 eta) z (L - z)
+                - sum_{n odd} (4 rho g L^2 / (eta pi^3 n^3)) sin(n pi z / L) exp(-n^2 pi^2 nu t / L^2)
+with eta = 8.700, the SRD kinetic + collisional closed form of the transport theory the
+paper cites (0.486 + 8.214 at these parameters).
+
+* The stated workload: a 128^3 box (20,971,520 particles), g = 1e-3, 20,000 steps, the
+  profile v_x(z) averaged over the last 2,000 steps in 128 slabs.  At t = 2,000 the flow
+  is still developing (the slowest mode decays over L^2 / (pi^2 nu) = 1,908), so it is
+  compared with the transient form above, averaged over the same window.
+* The accuracy variant: g = 1e-4 (peak velocity 0.24, well below the speed of sound) in a
+  32 x 32 x 128 channel, 140,000 steps (over seven decay times): the steady parabola's
+  viscosity within 2 % of 8.700.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+ETA_SRD = 8.700  # N_c 10, h 0.1, alpha 130 deg
+
+
+def closed_form(z, t, L, g, eta, rho=10.0, modes=401):
+    nu = eta / rho
+    v = rho * g / (2 * eta) * z * (L - z)
+    for n in range(1, modes + 1, 2):
+        v = v - (4 * rho * g * L**2 / (eta * np.pi**3 * n**3) * np.sin(n * np.pi * z / L)
+                 * np.exp(-(n * np.pi) ** 2 * nu * t / L**2))
+    return v
+
+
+def slab_average(f, L, nbins, npts=8):
+    """average of f(z) over each of nbins equal slabs of [0, L) (Gauss-Legendre)"""
+    x, w = np.polynomial.legendre.leggauss(npts)
+    edges = np.linspace(0.0, L, nbins + 1)
+    a, b = edges[:-1, None], edges[1:, None]
+    z = 0.5 * (b - a) * x[None, :] + 0.5 * (a + b)
+    return (f(z) * w[None, :]).sum(axis=1) / 2.0
+
+
+def run_channel(Lxy, Lz, g, steps, window, every, seed):
+    import torch
+
+    import paper_2406_15236_gb300 as mpc
+
+    torch.cuda.set_device(0)
+    sim = mpc.Simulation(L=(Lxy, Lxy, Lz), n_c=10.0, h=0.1, alpha_deg=130.0, variant=0,
+                         thermostat=1, walls_z=1, gravity=(g, 0.0, 0.0), seed=seed)
+    sim.step(steps - window)
+    counts = np.zeros(Lz)
+    vsum = np.zeros((Lz, 3))
+    times = []
+    for k in range(window // every):
+        sim.step(every)
+        c, v = sim.velocity_profile(Lz)
+        counts += c
+        vsum += v
+        times.append(steps - window + (k + 1) * every)
+    assert sim.get_state()[3] == steps
+    sim.close()
+    return vsum[:, 0] / counts, counts, np.asarray(times) * 0.1
+
+
+def fit_eta(v, times, L, g):
+    from scipy.optimize import minimize_scalar
+
+    def model(eta):
+        return np.mean([slab_average(lambda z: closed_form(z, t, L, g, eta), L, len(v)) for t in times],
+                       axis=0)
+
+    res = minimize_scalar(lambda eta: ((model(eta) - v) ** 2).sum(), bounds=(5.0, 15.0),
+                          method="bounded", options={"xatol": 1e-4})
+    return res.x, model
+
+
+def test_config2_poiseuille_128_transient_profile():
+    L, g = 128, 1e-3
+    v, counts, times = run_channel(L, L, g, 20000, 2000, 10, seed=2)
+    # the sample times stand in for the window: every tenth step of its 2,000
+    ref = np.mean([slab_average(lambda z: closed_form(z, t, L, g, ETA_SRD), L, L) for t in times[::4]],
+                  axis=0)
+    vc = ref[L // 2]
+    err = v - ref
+    rms, worst = np.sqrt((err**2).mean()) / vc, np.abs(err).max() / vc
+    eta_fit, _ = fit_eta(v, times[::4], L, g)
+    print(f"config 2 (L = 128, g = 1e-3, 20,000 steps): centre v_x {v[L // 2 - 1:L // 2 + 1].mean():.4f} "
+          f"vs closed form {vc:.4f}; profile error rms {rms:.2%}, max {worst:.2%} of the centre "
+          f"velocity; fitted eta {eta_fit:.3f} ({eta_fit / ETA_SRD - 1:+.2%} vs 8.700); "
+          f"particles per slab {counts.mean() / len(times):.0f}")
+    assert np.all(counts > 0)
+    assert rms < 0.015 and worst < 0.025
+    assert abs(eta_fit / ETA_SRD - 1.0) < 0.02
+
+
+def test_poiseuille_steady_parabola_viscosity():
+    L, g = 128, 1e-4
+    v, counts, times = run_channel(32, L, g, 140000, 40000, 20, seed=5)
+    eta_fit, model = fit_eta(v, times[::50], L, g)
+    # the same fit over the bulk only (two slabs next to each wall left out)
+    z = np.arange(L) + 0.5
+    inner = (z > 2) & (z < L - 2)
+    c = np.polyfit(z[inner], v[inner], 2)
+    eta_curv = -10.0 * g / (2 * c[0])
+    resid = v - model(eta_fit)
+    print(f"g = 1e-4 channel (32 x 32 x 128, 140,000 steps): eta from the profile {eta_fit:.3f} "
+          f"({eta_fit / ETA_SRD - 1:+.2%}), from the bulk curvature {eta_curv:.3f} "
+          f"({eta_curv / ETA_SRD - 1:+.2%}); residual rms {np.sqrt((resid**2).mean()):.2e} "
+          f"of peak {v.max():.4f}")
+    assert abs(eta_fit / ETA_SRD - 1.0) < 0.02
+    assert abs(eta_curv / ETA_SRD - 1.0) < 0.02
