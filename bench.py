@@ -62,7 +62,9 @@ def parse_args(argv=None):
     ap.add_argument("--batch-boxes", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=100)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
-    ap.add_argument("--serve-jobs", type=int, default=24)
+    ap.add_argument("--serve-jobs", type=int, default=200)
+    ap.add_argument("--serve-step-scale", type=float, default=0.1,
+                    help="job step counts are the stated log-uniform 1k-20k times this factor")
     return ap.parse_args(argv)
 
 
@@ -406,10 +408,11 @@ def run_batched(args, mpc, torch) -> dict:
 
 # --- serving ---------------------------------------------------------------------------------------
 
-def serving_trace(n: int, rate: float, seed: int):
+def serving_trace(n: int, rate: float, seed: int, step_scale: float = 1.0):
     """Viscosity-measurement jobs with Poisson arrivals (mean `rate` per s, the first at
     t = 0): periodic box, L uniform in {16, ..., 96}, N_c = 10, variant / alpha / h as in
-    the batched ensemble, steps log-uniform in [1000, 20000], seeds 5000 + i."""
+    the batched ensemble, steps log-uniform in [1000, 20000] times step_scale, seeds
+    5000 + i."""
     import numpy as np
 
     rng = np.random.default_rng(seed)
@@ -417,7 +420,8 @@ def serving_trace(n: int, rate: float, seed: int):
     Ls = rng.integers(16, 97, n)
     kinds = rng.integers(0, len(BATCH_KINDS), n)
     hs = rng.choice([0.02, 0.05, 0.1], n)
-    steps = np.exp(rng.uniform(np.log(1000.0), np.log(20000.0), n)).astype(int)
+    steps = np.maximum(1, (step_scale * np.exp(rng.uniform(np.log(1000.0), np.log(20000.0), n)))
+                       .astype(int))
     jobs = []
     for i in range(n):
         name, alpha = BATCH_KINDS[int(kinds[i])]
@@ -442,9 +446,32 @@ def serve_once(mpc, jobs, budget, sequential: bool, **policy) -> dict:
     return {"jobs_done": len(done), "jobs_failed": len(res) - len(done),
             "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)),
+            "p99_ci95_s": bootstrap_ci(lat, 99),
             "mean_latency_s": float(lat.mean()), "makespan_s": makespan,
             "jobs_per_s": len(done) / makespan, "particle_steps_per_s": work / makespan,
-            "loop": None if sequential else stats}
+            "loop": None if sequential else stats, "latencies_s": [round(float(x), 4) for x in lat]}
+
+
+def bootstrap_ci(x, q, n=2000, seed=0):
+    """95 % bootstrap interval of the q-th percentile of x (resampling the jobs)"""
+    import numpy as np
+
+    rng = np.random.default_rng(seed)
+    x = np.asarray(x)
+    qs = np.percentile(x[rng.integers(0, len(x), (n, len(x)))], q, axis=1)
+    return [float(np.percentile(qs, 2.5)), float(np.percentile(qs, 97.5))]
+
+
+def paired_p99_ratio_ci(a, b, n=2000, seed=1):
+    """95 % bootstrap interval of p99(a) / p99(b) for latencies of the same jobs (resampled
+    together)"""
+    import numpy as np
+
+    rng = np.random.default_rng(seed)
+    a, b = np.asarray(a), np.asarray(b)
+    idx = rng.integers(0, len(a), (n, len(a)))
+    r = np.percentile(a[idx], 99, axis=1) / np.percentile(b[idx], 99, axis=1)
+    return [float(np.percentile(r, 2.5)), float(np.percentile(r, 97.5))]
 
 
 def run_serving(args, mpc) -> dict:

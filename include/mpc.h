@@ -212,7 +212,9 @@ mpc_status mpc_profile_step_kernel(mpc_handle h, double* mean_ms, int32_t* sampl
  * inputs.  Positions outside [0, L << F) are rejected with MPC_EINVAL before sorting.
  * stream: cudaStream_t or NULL; the call synchronises it before returning.
  * The first call on a device looks up the scratch area's device address for that
- * device (cudaGetSymbolAddress); make that first call before any stream capture.
+ * device (cudaGetSymbolAddress); make that first call before any stream capture.  The
+ * address is kept for the rest of the process: resetting a device (cudaDeviceReset) in
+ * a process that has called this entry point on it is not supported.
  * All calls in the process share the one scratch area: calls that overlap on the GPU
  * (different streams or threads, not ordered) race and corrupt each other's results.
  * Errors are reported through mpc_last_error(NULL). */
@@ -354,8 +356,16 @@ enum {
                                      results do not depend on the other jobs */
   MPC_SERVER_SEQUENTIAL = 2u,     /* one job at a time on the plain single-box path */
   MPC_SERVER_SHARE_ALL = 4u,      /* every resident job steps in every chunk */
-  MPC_SERVER_FIRST_COME = 8u      /* pick stepping jobs in arrival order instead of by
+  MPC_SERVER_FIRST_COME = 8u,     /* pick stepping jobs in arrival order instead of by
                                      least remaining work */
+  MPC_SERVER_AGED = 16u,          /* pick stepping jobs by remaining time (at the
+                                     measured particle-step rate) minus the time waited
+                                     since arrival: least remaining work for fresh jobs,
+                                     arrival order for jobs that have waited as long as
+                                     they still need */
+  MPC_SERVER_BACKFILL = 32u       /* jobs of at most a sixteenth of the fill step in every
+                                     chunk, beyond the fill: small jobs progress beside a
+                                     large one at little cost to it */
 };
 /* By default a chunk steps the resident jobs with the least remaining work (steps x
  * particles) until they hold fill_kparticles thousand particles (default 16M: enough

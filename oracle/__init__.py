@@ -107,6 +107,8 @@ def lib():
             L.orc_phantoms.argtypes = [P(Params), i64, u32, f64, ctypes.c_int, P(f64), P(f64),
                                        P(f64)]
             L.orc_phantoms.restype = ctypes.c_int
+            L.orc_phantom_particles.argtypes = [P(Params), i64, u32, u32, ctypes.c_int,
+                                                ctypes.c_int32, P(f64), P(f64), P(f64)]
             L.orc_sample_normal.argtypes = [ctypes.c_uint64, i64, P(f64)]
             L.orc_sample_gamma.argtypes = [ctypes.c_uint64, f64, i64, P(f64)]
             L.orc_sample_poisson.argtypes = [ctypes.c_uint64, f64, i64, P(ctypes.c_int32)]
@@ -267,6 +269,16 @@ def phantoms(p: Params, step_index: int, cell: int, phi: float, wall: int):
     fl = lib().orc_phantoms(ctypes.byref(p), step_index, cell, phi, wall, _ptr(nph, ctypes.c_double),
                             _ptr(P, ctypes.c_double), _ptr(K, ctypes.c_double))
     return int(nph[0]), P, float(K[0]), fl
+
+
+def phantom_particles(p: Params, step_index: int, cell: int, Sz: int, wall: int, k: int):
+    """k phantom particles of a wall-cut cell, one by one: positions relative to the cell
+    centre (k, 3), velocities (k, 3), random velocities (k, 3)"""
+    rho, v, vr = (np.zeros((max(k, 1), 3)) for _ in range(3))
+    lib().orc_phantom_particles(ctypes.byref(p), step_index, cell, Sz, wall, k,
+                                _ptr(rho, ctypes.c_double), _ptr(v, ctypes.c_double),
+                                _ptr(vr, ctypes.c_double))
+    return rho[:k], v[:k], vr[:k]
 
 
 def max_eigenvalue_sym3(A) -> float:

@@ -33,6 +33,7 @@
 #define TAG_ATV 6u
 #define TAG_INITX 7u
 #define TAG_INITV 8u
+#define TAG_PHPART 9u
 #define TAG_TEST 15u
 
 #define GAMMA_MAX_ATTEMPTS 32
@@ -515,6 +516,46 @@ int orc_phantoms(const orc_params* p, int64_t step, uint32_t cell, double phi, i
   return flags;
 }
 
+/* Phantom particles of a wall-cut cell one by one, for the angular-momentum-conserving
+ * variants, whose collision needs every member's position (Sec. II, "Boundary
+ * conditions"; positions drawn uniformly in the wall part of the cell).  The count k is
+ * orc_phantoms' count for the same cell and step.  Phantom j draws Philox(cell, step,
+ * TAG_PHPART, 3j + q): q = 0 its position on the fixed-point grid of the cell -- x and y
+ * uniform over the cell, z uniform over the part beyond the wall (local coordinate below
+ * the lattice shift Sz at the bottom wall, at or above it at the top wall) --, q = 1, 2 six
+ * standard normals by Box-Muller: its velocity u_wall x + sqrt(kT/m) (n0, n1, n2) and its
+ * random velocity sqrt(kT/m) (n3, n4, n5).  rho (3k): positions relative to the cell
+ * centre; v, vran (3k).  wall: 0 bottom (z = 0), 1 top (z = Lz). */
+void orc_phantom_particles(const orc_params* p, int64_t step, uint32_t cell, uint32_t Sz, int wall,
+                           int32_t k, double* rho, double* v, double* vran) {
+  const int F = orc_fixed_bits(p);
+  const uint64_t one = (uint64_t)1 << F;
+  const double inv2F = ldexp(1.0, -F), sigma = sqrt(p->kT / p->m);
+  for (int32_t j = 0; j < k; ++j) {
+    uint32_t a[4], b[4], c[4];
+    draw(p, cell, (uint32_t)step, TAG_PHPART, 3u * (uint32_t)j, a);
+    draw(p, cell, (uint32_t)step, TAG_PHPART, 3u * (uint32_t)j + 1u, b);
+    draw(p, cell, (uint32_t)step, TAG_PHPART, 3u * (uint32_t)j + 2u, c);
+    const uint64_t ix = a[0] >> (32 - F), iy = a[1] >> (32 - F);
+    const uint64_t iz = wall == 0 ? (((uint64_t)a[2] * (uint64_t)Sz) >> 32)
+                                  : (uint64_t)Sz + (((uint64_t)a[2] * (one - (uint64_t)Sz)) >> 32);
+    const double half = (double)(one >> 1);
+    rho[3 * j + 0] = ((double)ix - half) * inv2F;
+    rho[3 * j + 1] = ((double)iy - half) * inv2F;
+    rho[3 * j + 2] = ((double)iz - half) * inv2F;
+    double n0, n1, n2, n3, n4, n5;
+    box_muller(uniform01(b[0]), uniform01(b[1]), &n0, &n1);
+    box_muller(uniform01(b[2]), uniform01(b[3]), &n2, &n3);
+    box_muller(uniform01(c[0]), uniform01(c[1]), &n4, &n5);
+    v[3 * j + 0] = p->wall_u[wall] + sigma * n0;
+    v[3 * j + 1] = sigma * n1;
+    v[3 * j + 2] = sigma * n2;
+    vran[3 * j + 0] = sigma * n3;
+    vran[3 * j + 1] = sigma * n4;
+    vran[3 * j + 2] = sigma * n5;
+  }
+}
+
 /* ------------------------------------------------------------------------------ */
 
 int orc_init(const orc_params* p, int64_t N, uint32_t* X, double* V, uint32_t* id) {
@@ -651,43 +692,74 @@ int orc_step(const orc_params* p, int64_t N, uint32_t* X, double* V, const uint3
         if (sens_out) sens_out[i] = 0.0;
       }
     } else {
-      /* angular-momentum-conserving variants: centre-of-mass frame of the cell */
-      double vcm[3];
-      for (int a = 0; a < 3; ++a) vcm[a] = sumv[a] / (double)n;
-      double* rk = (double*)malloc(sizeof(double) * 3 * (size_t)n);
-      double* wk = (double*)malloc(sizeof(double) * 3 * (size_t)n);
-      double* dv = (double*)malloc(sizeof(double) * 3 * (size_t)n);
-      double* sk = (double*)malloc(sizeof(double) * (size_t)n);
-      if (!rk || !wk || !dv || !sk) return -1;
+      /* angular-momentum-conserving variants: centre-of-mass frame of the cell.  In a
+       * cell cut by a no-slip wall the members are the fluid particles and the phantom
+       * particles of the wall part (orc_phantom_particles); only the fluid ones are
+       * updated. */
+      int32_t kph = 0;
+      uint32_t Sz = S[2];
+      int wall = 0;
+      if (p->walls_z == 1) {
+        int64_t cz = c / ((int64_t)p->L[0] * p->L[1]);
+        double s_frac = (double)S[2] * g.inv2F;
+        double phi = -1.0;
+        if (cz == 0) phi = s_frac;
+        else if (cz == p->L[2]) { phi = 1.0 - s_frac; wall = 1; }
+        if (phi >= 0.0) {
+          double nph, Pph[3], Kint;
+          flags |= orc_phantoms(p, step, (uint32_t)c, phi, wall, &nph, Pph, &Kint);
+          kph = (int32_t)nph;
+        }
+      }
+      const int64_t nt = n + kph;  /* all members */
+      double* rk = (double*)malloc(sizeof(double) * 3 * (size_t)nt);
+      double* vk = (double*)malloc(sizeof(double) * 3 * (size_t)nt);
+      double* ran = (double*)malloc(sizeof(double) * 3 * (size_t)nt);
+      double* wk = (double*)malloc(sizeof(double) * 3 * (size_t)nt);
+      double* dv = (double*)malloc(sizeof(double) * 3 * (size_t)nt);
+      double* sk = (double*)malloc(sizeof(double) * (size_t)nt);
+      if (!rk || !vk || !ran || !wk || !dv || !sk) return -1;
       for (int64_t k = 0; k < n; ++k)
-        for (int a = 0; a < 3; ++a) rk[3 * k + a] = rho[3 * mem[k] + a];
+        for (int a = 0; a < 3; ++a) {
+          rk[3 * k + a] = rho[3 * mem[k] + a];
+          vk[3 * k + a] = vb[3 * mem[k] + a];
+        }
+      if (kph > 0)
+        orc_phantom_particles(p, step, (uint32_t)c, Sz, wall, kph, rk + 3 * n, vk + 3 * n, ran + 3 * n);
+      double vcm[3] = {0, 0, 0};
+      for (int64_t k = 0; k < nt; ++k)
+        for (int a = 0; a < 3; ++a) vcm[a] += vk[3 * k + a];
+      for (int a = 0; a < 3; ++a) vcm[a] /= (double)nt;
       double vrm[3] = {0, 0, 0};
       if (p->variant == ORC_AT_A) {
         /* MPC-AT+a: v_i' = v_cm + v_i^ran - <v^ran> + omega x r_ic, with
-         * omega = J^{-1} sum_j r_jc x (v_j - v_j^ran), v^ran ~ N(0, kT/m) per component;
-         * dv holds v^ran */
+         * omega = J^{-1} sum_j r_jc x (v_j - v_j^ran), v^ran ~ N(0, kT/m) per component
+         * (fluid particles keyed by their id) */
         for (int64_t k = 0; k < n; ++k) {
           uint32_t r[4];
           draw(p, id[mem[k]], (uint32_t)step, TAG_ATV, 0u, r);
           double z0, z1, z2, z3;
           box_muller(uniform01(r[0]), uniform01(r[1]), &z0, &z1);
           box_muller(uniform01(r[2]), uniform01(r[3]), &z2, &z3);
-          dv[3 * k + 0] = sigma * z0;
-          dv[3 * k + 1] = sigma * z1;
-          dv[3 * k + 2] = sigma * z2;
-          for (int a = 0; a < 3; ++a) vrm[a] += dv[3 * k + a];
+          ran[3 * k + 0] = sigma * z0;
+          ran[3 * k + 1] = sigma * z1;
+          ran[3 * k + 2] = sigma * z2;
         }
-        for (int a = 0; a < 3; ++a) vrm[a] /= (double)n;
-        for (int64_t k = 0; k < n; ++k)
-          for (int a = 0; a < 3; ++a) wk[3 * k + a] = vb[3 * mem[k] + a] - dv[3 * k + a];
+        for (int64_t k = 0; k < nt; ++k)
+          for (int a = 0; a < 3; ++a) {
+            vrm[a] += ran[3 * k + a];
+            wk[3 * k + a] = vk[3 * k + a] - ran[3 * k + a];
+            dv[3 * k + a] = ran[3 * k + a];
+          }
+        for (int a = 0; a < 3; ++a) vrm[a] /= (double)nt;
       } else {
         /* MPC-SRD+a, Eqs. (3)-(4): v_i' = v_cm + D v_ic + omega x r_ic with
          * omega = m I^{-1} sum_i r_ic x (v_ic - D v_ic); dv holds D v_ic */
         double axis[3];
         orc_srd_axis(p, step, (uint32_t)c, axis);
-        for (int64_t k = 0; k < n; ++k) {
+        for (int64_t k = 0; k < nt; ++k) {
           double vic[3], rot[3];
-          for (int a = 0; a < 3; ++a) vic[a] = vb[3 * mem[k] + a] - vcm[a];
+          for (int a = 0; a < 3; ++a) vic[a] = vk[3 * k + a] - vcm[a];
           orc_rotate(axis, alpha, vic, rot);
           for (int a = 0; a < 3; ++a) {
             dv[3 * k + a] = rot[a];
@@ -696,7 +768,7 @@ int orc_step(const orc_params* p, int64_t N, uint32_t* X, double* V, const uint3
         }
       }
       double omega[3], rcm[3];
-      flags |= orc_cell_omega(n, rk, wk, omega, rcm, sens_out ? sk : NULL);
+      flags |= orc_cell_omega(nt, rk, wk, omega, rcm, sens_out ? sk : NULL);
       for (int64_t k = 0; k < n; ++k) {
         int64_t i = mem[k];
         double r[3], wxr[3];
@@ -710,7 +782,7 @@ int orc_step(const orc_params* p, int64_t N, uint32_t* X, double* V, const uint3
         }
         if (sens_out) sens_out[i] = sk[k];
       }
-      free(rk); free(wk); free(dv); free(sk);
+      free(rk); free(vk); free(ran); free(wk); free(dv); free(sk);
     }
     if (cell_flags) cell_flags[c] = (uint8_t)flags;
   }

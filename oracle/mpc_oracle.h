@@ -96,6 +96,8 @@ int orc_cell_omega(int64_t n, const double* rho, const double* w, double omega[3
                    double rcm[3], double* sens);
 int orc_phantoms(const orc_params* p, int64_t step, uint32_t cell, double phi, int wall,
                  double* nph, double P[3], double* Kint);
+void orc_phantom_particles(const orc_params* p, int64_t step, uint32_t cell, uint32_t Sz, int wall,
+                           int32_t k, double* rho, double* v, double* vran);
 void orc_sample_normal(uint64_t seed, int64_t n, double* out);
 void orc_sample_gamma(uint64_t seed, double shape, int64_t n, double* out);
 void orc_sample_poisson(uint64_t seed, double lambda, int64_t n, int32_t* out);

@@ -92,6 +92,8 @@ class mpc_batch_info(ctypes.Structure):
 
 MPC_SERVER_DETERMINISTIC, MPC_SERVER_SEQUENTIAL, MPC_SERVER_SHARE_ALL = 1, 2, 4
 MPC_SERVER_FIRST_COME = 8
+MPC_SERVER_AGED = 16
+MPC_SERVER_BACKFILL = 32
 MPC_JOB_QUEUED, MPC_JOB_RUNNING, MPC_JOB_DONE, MPC_JOB_FAILED = 0, 1, 2, 3
 MPC_JOB_KEEP_SERIES, MPC_JOB_KEEP_STATE = 1, 2
 
@@ -661,7 +663,7 @@ class Server:
 
     def __init__(self, hbm_budget_bytes, chunk_steps=0, max_active=0, deterministic=False,
                  sequential=False, share_all=False, first_come=False, fill_kparticles=0,
-                 stream=None):
+                 aged=False, backfill=False, stream=None):
         import torch
 
         cfg = mpc_server_config()
@@ -671,7 +673,8 @@ class Server:
         cfg.flags = (MPC_SERVER_DETERMINISTIC if deterministic else 0) | \
             (MPC_SERVER_SEQUENTIAL if sequential else 0) | \
             (MPC_SERVER_SHARE_ALL if share_all else 0) | \
-            (MPC_SERVER_FIRST_COME if first_come else 0)
+            (MPC_SERVER_FIRST_COME if first_come else 0) | \
+            (MPC_SERVER_AGED if aged else 0) | (MPC_SERVER_BACKFILL if backfill else 0)
         cfg.fill_kparticles = int(fill_kparticles)
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream

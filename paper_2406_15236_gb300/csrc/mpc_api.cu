@@ -134,8 +134,6 @@ mpc_status validate(const mpc_params* p) {
     return fail(nullptr, MPC_EINVAL, "the MBS thermostat applies to SRD only");
   if (p->walls_z < 0 || p->walls_z > 2)
     return fail(nullptr, MPC_EINVAL, "walls_z must be 0 (periodic), 1 (no-slip) or 2 (slip)");
-  if (p->walls_z && p->variant != MPC_SRD)
-    return fail(nullptr, MPC_EINVAL, "walls are supported with SRD only");
   for (int k = 0; k < 2; ++k) {
     if (!std::isfinite(p->wall_u[k])) return fail(nullptr, MPC_EINVAL, "wall_u must be finite");
     if (p->wall_u[k] != 0.0 && p->walls_z != 1)

@@ -18,7 +18,7 @@ namespace mpc {
 // keying contract.
 enum : uint32_t {
   kTagShift = 1, kTagAxis = 2, kTagMbs = 3, kTagPhantom = 4, kTagPhGamma = 5,
-  kTagAtVel = 6, kTagInitX = 7, kTagInitV = 8
+  kTagAtVel = 6, kTagInitX = 7, kTagInitV = 8, kTagPhPart = 9
 };
 
 // Philox4x32-10 (Salmon et al., SC'11): per round, the two multiplier words give
@@ -122,6 +122,41 @@ __device__ __forceinline__ int poisson_inv(double u, double lambda) {
     cdf += prob;
   }
   return k;
+}
+
+// Phantom particle j of the wall-cut collision cell cg (the angular-momentum-conserving
+// variants at no-slip walls, Sec. II "Boundary conditions"; the oracle draws the same
+// particles from the same counters): its position relative to the cell centre on the
+// fixed-point grid (integers, units 2^-F) -- x and y uniform over the cell, z uniform over
+// the part beyond the wall (local coordinate below the shift Sz at the bottom wall, from Sz
+// up at the top) --, its velocity u_wall x + sigma (n0, n1, n2) and random velocity
+// sigma (n3, n4, n5), from Philox(cg, step, kTagPhPart, 3j + q), q = 0, 1, 2.
+struct PhantomParticle {
+  int ix, iy, iz;
+  float vx, vy, vz, ux, uy, uz;
+};
+
+__device__ __forceinline__ PhantomParticle phantom_particle(const Geom& g, uint32_t cg, uint32_t step,
+                                                            int j, uint32_t Sz, int wall) {
+  const uint4 a = draw(g, cg, step, kTagPhPart, 3u * (uint32_t)j);
+  const uint4 b = draw(g, cg, step, kTagPhPart, 3u * (uint32_t)j + 1u);
+  const uint4 c = draw(g, cg, step, kTagPhPart, 3u * (uint32_t)j + 2u);
+  const uint32_t one = 1u << g.F, half = one >> 1;
+  const uint32_t ix = a.x >> (32 - g.F), iy = a.y >> (32 - g.F);
+  const uint32_t iz = wall == 0 ? (uint32_t)(((uint64_t)a.z * Sz) >> 32)
+                                : Sz + (uint32_t)(((uint64_t)a.z * (uint64_t)(one - Sz)) >> 32);
+  const float2 n01 = normal2(b.x, b.y), n23 = normal2(b.z, b.w), n45 = normal2(c.x, c.y);
+  PhantomParticle q;
+  q.ix = (int)ix - (int)half;
+  q.iy = (int)iy - (int)half;
+  q.iz = (int)iz - (int)half;
+  q.vx = g.wall_u[wall] + g.sigma * n01.x;
+  q.vy = g.sigma * n01.y;
+  q.vz = g.sigma * n23.x;
+  q.ux = g.sigma * n23.y;
+  q.uy = g.sigma * n45.x;
+  q.uz = g.sigma * n45.y;
+  return q;
 }
 
 __device__ __forceinline__ uint3 lattice_shift(const Geom& g, uint32_t step) {

@@ -44,7 +44,8 @@ mpc_status fail(mpc_status st, const std::string& msg) {
   return st;
 }
 
-// device address of the scratch array on the current device (set up on first use)
+// device address of the scratch array on the current device (set up on first use and
+// kept for the life of the process: a device reset after that first call is not supported)
 mpc_status scratch_for_current_device(uint32_t** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);

@@ -5,7 +5,8 @@
 // step count (their observables become a Green-Kubo viscosity, their memory returns to
 // the arena once the queued work is past it), picks the resident jobs that step in the
 // next chunk (by default the least remaining work first, or the oldest first, until the
-// GPU is full; the others hold through their step limits), and enqueues the chunk, sized
+// GPU is full, or by remaining time minus waiting time; the others hold through their
+// step limits), and enqueues the chunk, sized
 // so that the next stepping job to finish ends on the chunk boundary.  While a chunk runs, the loop keeps
 // admitting arrivals: box creation runs on the batch's side stream and overlaps the
 // chunk, and the new members join the next chunk.
@@ -54,7 +55,9 @@ struct mpc_server_s {
   mpc_server_config cfg{};
   cudaStream_t stream = nullptr;
   cudaStream_t side = nullptr;  // result copies that must not wait for queued chunks
-  bool det = false, sequential = false, share_all = false, first_come = false;
+  bool det = false, sequential = false, share_all = false, first_come = false, aged = false,
+       backfill = false;
+  double work_done = 0.0;  // particle-steps of the chunks run so far (aged ordering)
   int64_t fill = kFillParticles;
   int chunk = 100;
   mpc_batch batch = nullptr;
@@ -231,15 +234,30 @@ mpc_status run_batched(mpc_server s, double deadline) {
     std::vector<Job*> resident;  // (retired jobs await analysis with h = NULL)
     for (Job& j : s->jobs)
       if (j.res.status == MPC_JOB_RUNNING && j.h) resident.push_back(&j);
-    if (!s->first_come)
+    if (s->aged) {
+      // remaining time at the measured rate minus the time already waited: a fresh short
+      // job goes first, a job that has waited as long as it still needs overtakes it
+      const double rate = s->stats.gpu_ms > 0.0 ? s->work_done / (1e-3 * s->stats.gpu_ms) : 4e10;
+      const double t = now_s(s->t0);
+      auto key = [&](const Job* j) {
+        return (double)(j->spec.steps - j->h->target_step) * (double)j->h->N / rate -
+               (t - j->spec.arrival_s);
+      };
+      std::stable_sort(resident.begin(), resident.end(),
+                       [&](const Job* a, const Job* b) { return key(a) < key(b); });
+    } else if (!s->first_come) {
       std::stable_sort(resident.begin(), resident.end(), [](const Job* a, const Job* b) {
         const double wa = (double)(a->spec.steps - a->h->target_step) * (double)a->h->N;
         const double wb = (double)(b->spec.steps - b->h->target_step) * (double)b->h->N;
         return wa < wb;
-      });  // else arrival order (jobs are kept in arrival order)
+      });
+    }  // else arrival order (jobs are kept in arrival order)
     int64_t min_left = INT64_MAX, filled = 0;
+    double chunk_work = 0.0;  // particles stepping in this chunk
     for (Job* j : resident) {
-      const bool step = s->share_all || filled < s->fill;
+      // backfill: jobs of at most a sixteenth of the fill step whatever the others hold
+      const bool light = s->backfill && j->h->N * 16 <= s->fill;
+      const bool step = s->share_all || filled < s->fill || light;
       const int64_t want = step ? j->spec.steps : j->h->target_step;
       if (j->h->limit != want) {
         if (mpc_status st = mpc_set_step_limit(j->h, want); st != MPC_OK)
@@ -247,6 +265,7 @@ mpc_status run_batched(mpc_server s, double deadline) {
       }
       if (step) {
         filled += j->h->N;
+        chunk_work += (double)j->h->N;
         min_left = std::min(min_left, j->spec.steps - j->h->target_step);
       }
     }
@@ -263,6 +282,7 @@ mpc_status run_batched(mpc_server s, double deadline) {
       if (s->gap_open) s->stats.host_gap_ms += 1e3 * (now_s(s->t0) - s->gap_from);
       s->stats.chunks += 1;
       s->stats.chunk_steps += n;
+      s->work_done += chunk_work * (double)n;
     }
     // while the chunk runs: analyse the jobs retired after the previous chunk
     for (Job* j : fetched) analyse(s, *j);
@@ -358,7 +378,8 @@ mpc_status mpc_server_create(const mpc_server_config* cfg, void* stream, mpc_ser
   if (cfg->hbm_budget_bytes == 0 || cfg->chunk_steps < 0 || cfg->max_active < 0 ||
       cfg->max_active > kMaxBatchBoxes || cfg->fill_kparticles < 0 ||
       (cfg->flags & ~(uint32_t)(MPC_SERVER_DETERMINISTIC | MPC_SERVER_SEQUENTIAL |
-                                MPC_SERVER_SHARE_ALL | MPC_SERVER_FIRST_COME)))
+                                MPC_SERVER_SHARE_ALL | MPC_SERVER_FIRST_COME | MPC_SERVER_AGED |
+                                MPC_SERVER_BACKFILL)))
     return sfail(nullptr, MPC_EINVAL, "invalid server configuration");
   mpc_server s = new (std::nothrow) mpc_server_s();
   if (!s) return sfail(nullptr, MPC_ENOMEM, "host allocation failed");
@@ -368,6 +389,8 @@ mpc_status mpc_server_create(const mpc_server_config* cfg, void* stream, mpc_ser
   s->sequential = (cfg->flags & MPC_SERVER_SEQUENTIAL) != 0;
   s->share_all = (cfg->flags & MPC_SERVER_SHARE_ALL) != 0;
   s->first_come = (cfg->flags & MPC_SERVER_FIRST_COME) != 0;
+  s->aged = (cfg->flags & MPC_SERVER_AGED) != 0;
+  s->backfill = (cfg->flags & MPC_SERVER_BACKFILL) != 0;
   if (cfg->fill_kparticles > 0) s->fill = (int64_t)cfg->fill_kparticles * 1000;
   s->chunk = cfg->chunk_steps > 0 ? cfg->chunk_steps : 100;
   if (cudaEventCreate(&s->chunk_done) != cudaSuccess || cudaEventCreate(&s->chunk_start) != cudaSuccess ||

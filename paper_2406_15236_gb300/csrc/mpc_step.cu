@@ -656,9 +656,19 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
         }
       } else {
         // angular-momentum-conserving variants.  First pass: centre of mass and mean of
-        // w (AT+a: w = v - v_ran; SRD+a: w = v, so the mean is v_cm)
+        // w (AT+a: w = v - v_ran; SRD+a: w = v, so the mean is v_cm).  In a cell cut by a
+        // no-slip wall the phantom particles of the wall part are members too (drawn one
+        // by one: their positions enter the moments); the group's lanes share them like
+        // the fluid members
         float r0 = 0.f, r1 = 0.f, r2 = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f;
         constexpr bool kOnePass = VAR == 1 && !DET;
+        int nph = 0;
+        const int pwall = cz == 0 ? 0 : 1;
+        if (g.walls == 1 && exists && n > 0 && (cz == 0 || cz == g.L[2])) {
+          const double sz_ = (double)S0z * (double)g.inv2F;
+          const double phi = (cz == 0) ? sz_ : 1.0 - sz_;
+          nph = poisson_inv((double)u01(draw(g, cg, step, kTagPhantom, 0u).x), g.n_c * phi);
+        }
         float o_m[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if constexpr (DET) {
           // positions sum exactly as integers; velocities in fixed point
@@ -668,6 +678,14 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
             R0 += rho_int(g, sx[i], S0x); R1 += rho_int(g, sy[i], S0y);
             R2 += rho_int(g, sz[i] & ~kCrossedBit, S0z);
             const float v0 = svx[i], v1 = svy[i], v2 = svz[i];
+            fxbig = fmaxf(fxbig, fmaxf(fabsf(v0), fmaxf(fabsf(v1), fabsf(v2))));
+            W0 += to_fx(v0); W1 += to_fx(v1); W2 += to_fx(v2);
+          }
+          for (int j = sub; j < nph; j += tpc) {
+            const PhantomParticle q = phantom_particle(g, cg, step, j, S0z, pwall);
+            R0 += q.ix; R1 += q.iy; R2 += q.iz;
+            const float v0 = VAR == 1 ? q.vx - q.ux : q.vx, v1 = VAR == 1 ? q.vy - q.uy : q.vy,
+                        v2 = VAR == 1 ? q.vz - q.uz : q.vz;
             fxbig = fmaxf(fxbig, fmaxf(fabsf(v0), fmaxf(fabsf(v1), fabsf(v2))));
             W0 += to_fx(v0); W1 += to_fx(v1); W2 += to_fx(v2);
           }
@@ -690,6 +708,20 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
               o_m[6] += py * vz - pz * vy; o_m[7] += pz * vx - px * vz; o_m[8] += px * vy - py * vx;
             }
           }
+          for (int j = sub; j < nph; j += tpc) {
+            const PhantomParticle q = phantom_particle(g, cg, step, j, S0z, pwall);
+            const float px = (float)q.ix * g.inv2F, py = (float)q.iy * g.inv2F,
+                        pz = (float)q.iz * g.inv2F;
+            const float vx = VAR == 1 ? q.vx - q.ux : q.vx, vy = VAR == 1 ? q.vy - q.uy : q.vy,
+                        vz = VAR == 1 ? q.vz - q.uz : q.vz;
+            r0 += px; r1 += py; r2 += pz;
+            w0 += vx; w1 += vy; w2 += vz;
+            if constexpr (kOnePass) {
+              o_m[0] += px * px; o_m[1] += py * py; o_m[2] += pz * pz;
+              o_m[3] += px * py; o_m[4] += py * pz; o_m[5] += pz * px;
+              o_m[6] += py * vz - pz * vy; o_m[7] += pz * vx - px * vz; o_m[8] += px * vy - py * vx;
+            }
+          }
           r0 = group_sum(r0, tpc); r1 = group_sum(r1, tpc); r2 = group_sum(r2, tpc);
           w0 = group_sum(w0, tpc); w1 = group_sum(w1, tpc); w2 = group_sum(w2, tpc);
           if constexpr (kOnePass) {
@@ -697,7 +729,8 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
             for (int q = 0; q < 9; ++q) o_m[q] = group_sum(o_m[q], tpc);
           }
         }
-        const float inv = 1.0f / fmaxf((float)n, 1.0f);
+        const int nt = n + nph;  // members: fluid and phantom particles
+        const float inv = 1.0f / fmaxf((float)nt, 1.0f);
         const float rcx = r0 * inv, rcy = r1 * inv, rcz = r2 * inv;
         const float wmx = w0 * inv, wmy = w1 * inv, wmz = w2 * inv;
         // float AT+a takes the moments from the first pass's raw sums about the cell
@@ -709,13 +742,13 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
         float Lx = 0.f, Ly = 0.f, Lz = 0.f;
         bool second = true;
         if constexpr (kOnePass) {
-          const float fn = (float)n;
+          const float fn = (float)nt;
           Mxx = o_m[0] - fn * rcx * rcx; Myy = o_m[1] - fn * rcy * rcy; Mzz = o_m[2] - fn * rcz * rcz;
           Mxy = o_m[3] - fn * rcx * rcy; Myz = o_m[4] - fn * rcy * rcz; Mzx = o_m[5] - fn * rcz * rcx;
           Lx = o_m[6] - fn * (rcy * wmz - rcz * wmy);
           Ly = o_m[7] - fn * (rcz * wmx - rcx * wmz);
           Lz = o_m[8] - fn * (rcx * wmy - rcy * wmx);
-          second = n >= 2 && o_m[0] + o_m[1] + o_m[2] > 4.0f * (Mxx + Myy + Mzz);
+          second = nt >= 2 && o_m[0] + o_m[1] + o_m[2] > 4.0f * (Mxx + Myy + Mzz);
         }
         // SRD+a: the cell's random rotation axis (every lane of the group draws it)
         float ax = 0.f, ay = 0.f, az = 0.f;
@@ -734,12 +767,9 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
         float sLx = 0.f, sLy = 0.f, sLz = 0.f;
         long long qM[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // deterministic mode
         const bool any_second = !kOnePass || __any_sync(0xffffffffu, second && n > 0);
-        const int n2 = second ? n : 0;
-        for (int k = sub; any_second && k < n2; k += tpc) {
-          const int i = sperm[base + k];
-          const float rx = rho_axis(g, sx[i], S0x) - rcx, ry = rho_axis(g, sy[i], S0y) - rcy,
-                      rz = rho_axis(g, sz[i] & ~kCrossedBit, S0z) - rcz;
-          float wx = svx[i] - wmx, wy = svy[i] - wmy, wz = svz[i] - wmz;
+        // one member's terms about the centre of mass: r = rho - rho_cm, w - <w> (SRD+a:
+        // minus its rotation, Eq. 4)
+        auto second_term = [&](float rx, float ry, float rz, float wx, float wy, float wz) {
           if constexpr (VAR == 2) {
             const float nr = ax * wx + ay * wy + az * wz;
             const float t = (1.0f - g.cos_a) * nr;
@@ -759,6 +789,21 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
             sMxy += rx * ry; sMyz += ry * rz; sMzx += rz * rx;
             sLx += ry * wz - rz * wy; sLy += rz * wx - rx * wz; sLz += rx * wy - ry * wx;
           }
+        };
+        const int n2 = second ? n : 0;
+        for (int k = sub; any_second && k < n2; k += tpc) {
+          const int i = sperm[base + k];
+          second_term(rho_axis(g, sx[i], S0x) - rcx, rho_axis(g, sy[i], S0y) - rcy,
+                      rho_axis(g, sz[i] & ~kCrossedBit, S0z) - rcz, svx[i] - wmx, svy[i] - wmy,
+                      svz[i] - wmz);
+        }
+        const int nph2 = second ? nph : 0;
+        for (int j = sub; any_second && j < nph2; j += tpc) {
+          const PhantomParticle q = phantom_particle(g, cg, step, j, S0z, pwall);
+          const float vx = VAR == 1 ? q.vx - q.ux : q.vx, vy = VAR == 1 ? q.vy - q.uy : q.vy,
+                      vz = VAR == 1 ? q.vz - q.uz : q.vz;
+          second_term((float)q.ix * g.inv2F - rcx, (float)q.iy * g.inv2F - rcy,
+                      (float)q.iz * g.inv2F - rcz, vx - wmx, vy - wmy, vz - wmz);
         }
         if constexpr (DET) {
 #pragma unroll
@@ -779,7 +824,7 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
         }
         if (exists && n > 0 && sub == 0) {
           // J = tr(M) 1 - M (moment-of-inertia tensor per unit mass); omega = J^-1 L
-          const float3 om = solve_omega(n, Mxx, Myy, Mzz, Mxy, Myz, Mzx, Lx, Ly, Lz);
+          const float3 om = solve_omega(nt, Mxx, Myy, Mzz, Mxy, Myz, Mzx, Lx, Ly, Lz);
           const float ox_ = om.x, oy_ = om.y, oz_ = om.z;
           float* P = spar + lc;
           P[0 * bc] = wmx; P[1 * bc] = wmy; P[2 * bc] = wmz;

@@ -83,7 +83,7 @@ def test_struct_layouts_match_header(tmp_path):
 
 @pytest.mark.parametrize("bad", [dict(L=1), dict(L=(8, 8, 2000)), dict(h=0.0), dict(kT=-1.0),
                                  dict(n_c=0.0), dict(variant=7), dict(variant=1, thermostat=1),
-                                 dict(variant=1, walls_z=1), dict(capacity=-3),
+                                 dict(variant=2, thermostat=1, walls_z=1), dict(capacity=-3),
                                  dict(gravity=(float("nan"), 0.0, 0.0)),
                                  dict(tile_particles=-1), dict(tile_particles=20000),
                                  dict(threads_per_cell=3), dict(threads_per_cell=64),

@@ -76,6 +76,42 @@ def test_each_job_same_alone_and_in_the_mix(policy):
         assert r_one["eta_gk"] == r_mix["eta_gk"]
 
 
+@pytest.mark.parametrize("policy", [{}, {"aged": True}, {"share_all": True}])
+def test_each_job_same_alone_and_in_the_mix_float_mode(policy):
+    """Float mode (the default: float cell sums, whose order depends on the other boxes of a
+    launch): one step of every job of the trace, alone and in the mix, gives bit-identical
+    positions and velocities within the per-step bar of 1e-5 of each other (outside the
+    cells the oracle flags ill-conditioned); both runs also pass the oracle's per-step
+    check from the job's initial state."""
+    import oracle
+
+    mpc = _mpc()
+    jobs = [dict(j, steps=1, arrival_s=0.0) for j in TRACE]
+    budget = 8 << 30
+    mixed = _run(mpc, jobs, budget, **policy)
+    skip = oracle.FLAG_DEGENERATE | oracle.FLAG_MBS_NEAR_TIE | oracle.FLAG_POISSON_NEAR_TIE
+    worst = 0.0
+    for job, (r_mix, _, st_mix) in zip(jobs, mixed):
+        assert r_mix["status"] == mpc.MPC_JOB_DONE, r_mix
+        (r_one, _, st_one), = _run(mpc, [job], budget)
+        X1, V1, id1 = st_one
+        X2, V2, id2 = st_mix
+        assert np.array_equal(id1, id2) and np.array_equal(X1, X2), f"positions differ: {job}"
+        sim = mpc.Simulation(**_box_kw(job))
+        pre = sim.get_state()[:3]
+        sim.close()
+        p = par.oracle_params(**_box_kw(job))
+        ref = par.check_step(p, pre, st_one, 0, strict_flags=skip)["ref"]
+        par.check_step(p, pre, st_mix, 0, strict_flags=skip)
+        loose = (ref["flags"][ref["cell"]] & (skip | oracle.FLAG_ILL_CONDITIONED)) != 0
+        scale = np.maximum(np.linalg.norm(V1.astype(np.float64), axis=0), 1.0)
+        d = np.linalg.norm(V1.astype(np.float64) - V2, axis=0) / scale
+        worst = max(worst, float(d[~loose].max()))
+        assert d[~loose].max() <= par.VEL_TOL, f"velocities differ alone vs mixed: {job}"
+    print(f"float mode, alone vs mixed, one step: positions bit-identical, largest velocity "
+          f"difference {worst:.3g}")
+
+
 def test_admission_waits_for_memory():
     """With room for one job at a time, each job is admitted only after the previous one
     has been retired, and all finish."""

@@ -87,3 +87,114 @@ def test_aggregates_match_explicit_gaussian_particles():
         assert stats.ks_2samp(d[:, 1 + a], P_ex[:, a]).pvalue > 1e-3
     assert stats.ks_2samp(d[:, 4], K_ex).pvalue > 1e-3
     assert abs(d[:, 4].mean() - K_ex.mean()) < 0.05 * K_ex.mean()
+
+
+def test_phantom_particles_fill_the_wall_part():
+    """For the angular-momentum-conserving variants the phantoms are drawn one by one:
+    uniform positions in the part of the cell beyond the wall (x, y over the whole cell),
+    velocities N(u_wall, kT/m) and random velocities N(0, kT/m) per component; their
+    number is the count of the aggregate draw."""
+    p = oracle.params(L=(16, 16, 16), n_c=N_C, kT=KT, m=M, walls_z=1, variant=oracle.AT_A,
+                      seed=33, wall_u=U_WALL)
+    F = oracle.fixed_bits(p)
+    sig = np.sqrt(KT / M)
+    for wall, frac in ((0, 0.37), (1, 0.62)):
+        Sz = int(frac * 2**F)
+        s = Sz / 2.0**F
+        phi = s if wall == 0 else 1.0 - s
+        rho, v, vr = [], [], []
+        for c in range(3000):
+            k = oracle.phantoms(p, 2, c, phi, wall)[0]
+            r_, v_, u_ = oracle.phantom_particles(p, 2, c, Sz, wall, k)
+            rho.append(r_)
+            v.append(v_)
+            vr.append(u_)
+        rho, v, vr = np.concatenate(rho), np.concatenate(v), np.concatenate(vr)
+        lo, hi = (-0.5, s - 0.5) if wall == 0 else (s - 0.5, 0.5)
+        assert rho[:, 2].min() >= lo and rho[:, 2].max() < hi
+        assert stats.kstest(rho[:, 2], stats.uniform(lo, hi - lo).cdf).pvalue > 1e-3
+        for a in (0, 1):
+            assert stats.kstest(rho[:, a], stats.uniform(-0.5, 1.0).cdf).pvalue > 1e-3
+        assert stats.kstest((v[:, 0] - U_WALL[wall]) / sig, "norm").pvalue > 1e-3
+        for a in (1, 2):
+            assert stats.kstest(v[:, a] / sig, "norm").pvalue > 1e-3
+        for a in range(3):
+            assert stats.kstest(vr[:, a] / sig, "norm").pvalue > 1e-3
+        assert abs(len(rho) / 3000 - N_C * phi) < 4 * np.sqrt(N_C * phi / 3000)
+
+
+def _wall_cells_members(p, step, X_after, cell):
+    F = oracle.fixed_bits(p)
+    S = oracle.shift(p, step).astype(np.int64)
+    rho = (((X_after.astype(np.int64) + S[:, None]) & ((1 << F) - 1)) / 2.0**F - 0.5).T
+    Lx, Ly, Lz = p.L
+    cz = cell // (Lx * Ly)
+    return rho, cz, int(S[2])
+
+
+def _vran_fluid(p, ids, step):
+    """AT+a random velocities of fluid particles: Philox(id, step, tag 6) through
+    Box-Muller, restated in numpy from the published transform"""
+    sig = np.sqrt(p.kT / p.m)
+    out = np.zeros((len(ids), 3))
+    key = [p.seed & 0xFFFFFFFF, p.seed >> 32]
+    for i, pid in enumerate(ids):
+        r = oracle.philox([int(pid), step, 6 << 24, p.box], key)
+        u = (np.asarray(r, dtype=np.float64) // 512 + 0.5) / 2.0**23
+        R0, R1 = np.sqrt(-2 * np.log(u[0])), np.sqrt(-2 * np.log(u[2]))
+        out[i] = sig * np.array([R0 * np.cos(2 * np.pi * u[1]), R0 * np.sin(2 * np.pi * u[1]),
+                                 R1 * np.cos(2 * np.pi * u[3])])
+    return out
+
+
+@pytest.mark.parametrize("variant", [oracle.AT_A, oracle.SRD_A])
+def test_no_slip_wall_cells_conserve_momentum_and_angular_momentum_with_phantoms(variant):
+    """In a cell cut by a no-slip wall the collision acts on fluid and phantom particles
+    together: recomputing it in numpy from the members (np.linalg.solve for omega), the
+    fluid velocities match the oracle's, and the linear and angular momentum of all
+    members (the phantoms' post-collision velocities included) are conserved."""
+    p = oracle.params(L=(6, 6, 5), n_c=6.0, h=0.1, alpha_deg=120.0, variant=variant,
+                      walls_z=1, wall_u=(0.2, -0.1), seed=41)
+    X, V, ids = oracle.init(p)
+    step = 2
+    X, V, ids, _ = oracle.run(p, step, state=(X, V, ids))
+    r = oracle.step(p, X, V, ids, step, cells=True, counts=True, vpre=True, flags=True)
+    rho, cz, Sz = _wall_cells_members(p, step, r["X"], r["cell"])
+    F = oracle.fixed_bits(p)
+    s = Sz / 2.0**F
+    checked = 0
+    for c in np.flatnonzero(r["counts"] > 0):
+        czc = c // 36
+        if czc not in (0, p.L[2]) or r["flags"][c] & oracle.FLAG_DEGENERATE:
+            continue
+        wall = 0 if czc == 0 else 1
+        phi = s if wall == 0 else 1.0 - s
+        k = oracle.phantoms(p, step, int(c), phi, wall)[0]
+        if k == 0:
+            continue
+        rp, vp, up = oracle.phantom_particles(p, step, int(c), Sz, wall, k)
+        m_idx = np.flatnonzero(r["cell"] == c)
+        R = np.concatenate([rho[m_idx], rp])
+        Vb = np.concatenate([r["vpre"][:, m_idx].T, vp])
+        vcm = Vb.mean(axis=0)
+        rc = R.mean(axis=0)
+        q = R - rc
+        J = (q * q).sum() * np.eye(3) - q.T @ q
+        if variant == oracle.AT_A:
+            U = np.concatenate([_vran_fluid(p, ids[m_idx], step), up])
+            W = Vb - U
+            om = np.linalg.solve(J, np.cross(q, W).sum(axis=0))
+            new = vcm + U - U.mean(axis=0) + np.cross(om, q)
+        else:
+            ax = oracle.srd_axis(p, step, int(c))
+            D = np.array([oracle.rotate(ax, np.deg2rad(120.0), e) for e in np.eye(3)]).T
+            vic = Vb - vcm
+            W = vic - vic @ D.T
+            om = np.linalg.solve(J, np.cross(q, W).sum(axis=0))
+            new = vcm + vic @ D.T + np.cross(om, q)
+        np.testing.assert_allclose(new[: len(m_idx)], r["V"][:, m_idx].T, rtol=0, atol=1e-9)
+        np.testing.assert_allclose(new.sum(axis=0), Vb.sum(axis=0), rtol=0, atol=1e-9)
+        np.testing.assert_allclose(np.cross(q, new).sum(axis=0), np.cross(q, Vb).sum(axis=0),
+                                   rtol=0, atol=1e-9)
+        checked += 1
+    assert checked > 10
