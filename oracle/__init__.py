@@ -286,7 +286,7 @@ def max_eigenvalue_sym3(A) -> float:
     return lib().orc_max_eigenvalue_sym3(_ptr(a, ctypes.c_double))
 
 
-COND_FLOAT32 = 20.0  # cond(J) above which a cell is flagged FLAG_ILL_CONDITIONED
+COND_FLOAT32 = 10.0  # cond(J) above which a cell is flagged FLAG_ILL_CONDITIONED
 TIGHT_RMS = 0.05  # rms radius below which a cell of n >= 2 is flagged FLAG_ILL_CONDITIONED
 
 

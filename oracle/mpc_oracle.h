@@ -51,8 +51,9 @@ enum {
    *     rounds the entries of J by a relative u = 2^-24; that moves omega by ~u cond
    *     |omega|, and where L points along the weak axis omega itself grows like cond, so
    *     a member's velocity error grows like u cond^2 |L| |r| / lambda_max (about
-   *     1e-7 cond^2 / sqrt(n) in unit-temperature cells): below 1e-5 up to cond = 20.
-   *     About 0.2 % of the cells at N_c = 10.
+   *     1e-7 cond^2 / sqrt(n) in unit-temperature cells): near 1e-5 at cond = 20 (a
+   *     float32 kernel measured 1.2e-5 in a cell of cond 19.3), a quarter of that at the
+   *     threshold 10.  About 0.5 % of the cells at N_c = 10.
    * (b) n >= 2 members within ORC_TIGHT_RMS (rms) of their centre of mass.  Positions
    *     relative to the cell hold an absolute precision of u a; a cluster of radius
    *     0.05 a is resolved only to 20 u, which omega (growing like 1/radius) carries
@@ -61,7 +62,7 @@ enum {
   ORC_FLAG_DEGENERATE = 8       /* n >= 3 but det(J) <= 0: omega set to zero */
 };
 
-#define ORC_COND_FLOAT32 20.0
+#define ORC_COND_FLOAT32 10.0
 #define ORC_TIGHT_RMS 0.05
 
 /* observables slots (orc_step obs_out, 16 doubles) */

@@ -82,7 +82,7 @@ def test_srd_l16_every_step_100_steps():
 
 def test_at_a_per_step():
     """MPC-AT+a, N_c 10, h 0.05: every particle within 1e-5 except in the cells the oracle
-    flags ill-conditioned (cond(J) > 20), whose share is reported per step."""
+    flags ill-conditioned (cond(J) > 10), whose share is reported per step."""
     kw = dict(L=16, n_c=10.0, h=0.05, kT=1.0, variant=1, seed=3)
     log = []
     _run_parity(kw, 20, strict_flags=oracle.FLAG_DEGENERATE, log=log)
@@ -91,7 +91,7 @@ def test_at_a_per_step():
           f"1e-5 (all in them) {max(e['over_tol'] for e in log):.2e}; max error elsewhere "
           f"{max(e['max_err_strict'] for e in log):.3g}; largest error / (u sens) "
           f"{max(e['k_emp'] for e in log):.3g}")
-    assert max(ill) < 5e-3
+    assert max(ill) < 1e-2
 
 
 def _crafted_parity(kw, X, V, steps=1, log=None):
