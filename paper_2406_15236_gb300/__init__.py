@@ -94,6 +94,7 @@ MPC_SERVER_DETERMINISTIC, MPC_SERVER_SEQUENTIAL, MPC_SERVER_SHARE_ALL = 1, 2, 4
 MPC_SERVER_FIRST_COME = 8
 MPC_SERVER_AGED = 16
 MPC_SERVER_BACKFILL = 32
+MPC_SERVER_PRIORITY_HEAD = 64
 MPC_JOB_QUEUED, MPC_JOB_RUNNING, MPC_JOB_DONE, MPC_JOB_FAILED = 0, 1, 2, 3
 MPC_JOB_KEEP_SERIES, MPC_JOB_KEEP_STATE = 1, 2
 
@@ -663,7 +664,7 @@ class Server:
 
     def __init__(self, hbm_budget_bytes, chunk_steps=0, max_active=0, deterministic=False,
                  sequential=False, share_all=False, first_come=False, fill_kparticles=0,
-                 aged=False, backfill=False, stream=None):
+                 aged=False, backfill=False, priority_head=False, stream=None):
         import torch
 
         cfg = mpc_server_config()
@@ -674,7 +675,8 @@ class Server:
             (MPC_SERVER_SEQUENTIAL if sequential else 0) | \
             (MPC_SERVER_SHARE_ALL if share_all else 0) | \
             (MPC_SERVER_FIRST_COME if first_come else 0) | \
-            (MPC_SERVER_AGED if aged else 0) | (MPC_SERVER_BACKFILL if backfill else 0)
+            (MPC_SERVER_AGED if aged else 0) | (MPC_SERVER_BACKFILL if backfill else 0) | \
+            (MPC_SERVER_PRIORITY_HEAD if priority_head else 0)
         cfg.fill_kparticles = int(fill_kparticles)
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream

@@ -285,7 +285,8 @@ mpc_status refresh(mpc_batch b) {
   // its step limit is left out of the launches until its limit moves
   for (size_t i = 0; i < b->boxes.size() && !b->dirty; ++i) {
     const mpc_handle h = b->boxes[i];
-    if (b->gens[i] != h->buffers_gen || b->stepping[i] != (h->limit > h->target_step)) b->dirty = true;
+    if (b->gens[i] != h->buffers_gen || b->stepping[i] != (!h->detached && h->limit > h->target_step))
+      b->dirty = true;
   }
   if (!b->dirty) return MPC_OK;
   const int k = b->table_next;  // a pinned buffer whose previous upload has executed
@@ -296,17 +297,18 @@ mpc_status refresh(mpc_batch b) {
   std::vector<mpc_handle> packed;
   b->solo_args.clear();
   b->total_particles = 0;
-  t->nboxes = n;
+  int nt = 0;  // members the closing kernel advances (detached ones step on their own)
   for (int i = 0; i < n; ++i) {
     mpc_handle h = b->boxes[(size_t)i];
     b->gens[(size_t)i] = h->buffers_gen;
-    b->stepping[(size_t)i] = h->limit > h->target_step;
-    t->args[i] = step_args(h);
+    b->stepping[(size_t)i] = !h->detached && h->limit > h->target_step;
+    if (!h->detached) t->args[nt++] = step_args(h);
     b->total_particles += h->N;
     if (!b->stepping[(size_t)i]) continue;
-    if (!b->pack_all && h->g.nbricks >= b->solo_bricks) b->solo_args.push_back(t->args[i]);
+    if (!b->pack_all && h->g.nbricks >= b->solo_bricks) b->solo_args.push_back(t->args[nt - 1]);
     else packed.push_back(h);
   }
+  t->nboxes = nt;
   std::stable_sort(packed.begin(), packed.end(), [](mpc_handle x, mpc_handle y) {
     if (x->g.variant != y->g.variant) return x->g.variant < y->g.variant;
     const int tx = brick_tier(x->g), ty = brick_tier(y->g);
@@ -413,6 +415,16 @@ std::string class_key(const mpc_params& p) {
 }
 
 }  // namespace
+
+namespace mpc {
+namespace host {
+void batch_set_detached(mpc_handle h, bool detached) {
+  if (!h || h->detached == detached) return;
+  h->detached = detached;
+  if (h->batch) h->batch->dirty = true;
+}
+}  // namespace host
+}  // namespace mpc
 
 extern "C" {
 
@@ -657,6 +669,7 @@ mpc_status mpc_batch_remove(mpc_batch b, mpc_handle h) {
   return MPC_OK;
 }
 
+
 mpc_status mpc_batch_step(mpc_batch b, int64_t nsteps) {
   if (!b) return bfail(nullptr, MPC_EINVAL, "batch is NULL");
   if (nsteps < 0) return bfail(b, MPC_EINVAL, "nsteps must be >= 0");
@@ -664,7 +677,8 @@ mpc_status mpc_batch_step(mpc_batch b, int64_t nsteps) {
   if (nsteps == 0 || b->boxes.empty()) return MPC_OK;
   const auto t_plan = std::chrono::steady_clock::now();
   if (mpc_status st = refresh(b); st != MPC_OK) return st;
-  for (mpc_handle h : b->boxes) h->target_step += std::min(nsteps, h->limit - h->target_step);
+  for (mpc_handle h : b->boxes)
+    if (!h->detached) h->target_step += std::min(nsteps, h->limit - h->target_step);
   int64_t n = nsteps;
   // a plan used once (e.g. between admissions of a serving loop) is launched directly;
   // from its second use on it is captured

@@ -38,6 +38,8 @@ struct mpc_s {
   int recoveries = 0;
   size_t smem_limit = 0;
   mpc_batch_s* batch = nullptr;    // owning batch (members are destroyed through it)
+  bool detached = false;           // a batch member stepped on its own (left out of the
+                                   // batch's launches and closing kernel)
   uint64_t buffers_gen = 0;        // bumped whenever the particle buffers are reallocated
   // profiling: event pairs around step-kernel launches (graph nodes and single launches)
   bool profiling = false;
@@ -89,6 +91,9 @@ StepArgs step_args(mpc_handle h);
 mpc_status read_ctrl(mpc_handle h);
 mpc_status sync_and_repair(mpc_handle h);
 mpc_status set_step_limit(mpc_handle h, int64_t limit);
+// detaches a member from its batch's steps (the caller steps it with mpc_step on a stream
+// of its own) or attaches it again; the batch rebuilds its launch plan
+void batch_set_detached(mpc_handle h, bool detached);
 
 }  // namespace host
 }  // namespace mpc

@@ -56,7 +56,10 @@ struct mpc_server_s {
   cudaStream_t stream = nullptr;
   cudaStream_t side = nullptr;  // result copies that must not wait for queued chunks
   bool det = false, sequential = false, share_all = false, first_come = false, aged = false,
-       backfill = false;
+       backfill = false, priority_head = false;
+  cudaStream_t head_stream = nullptr;  // priority_head: the oldest job's own steps
+  cudaEvent_t head_done = nullptr;
+  Job* head = nullptr;
   double work_done = 0.0;  // particle-steps of the chunks run so far (aged ordering)
   int64_t fill = kFillParticles;
   int chunk = 100;
@@ -234,6 +237,25 @@ mpc_status run_batched(mpc_server s, double deadline) {
     std::vector<Job*> resident;  // (retired jobs await analysis with h = NULL)
     for (Job& j : s->jobs)
       if (j.res.status == MPC_JOB_RUNNING && j.h) resident.push_back(&j);
+    if (s->priority_head) {
+      // the oldest resident job steps on its own high-priority stream, outside the batch's
+      // launches: the GPU's block scheduler serves it first, the batch fills what it leaves
+      Job* oldest = resident.empty() ? nullptr : resident.front();  // arrival order
+      if (oldest != s->head) {
+        if (s->head && s->head->h) {
+          batch_set_detached(s->head->h, false);
+          s->head->h->stream = s->stream;
+        }
+        s->head = oldest;
+        if (oldest) {
+          oldest->h->stream = s->head_stream;
+          batch_set_detached(oldest->h, true);
+          if (mpc_status st = mpc_set_step_limit(oldest->h, oldest->spec.steps); st != MPC_OK)
+            return sfail(s, st, "step limit: " + oldest->h->err);
+        }
+      }
+      if (oldest) resident.erase(resident.begin());
+    }
     if (s->aged) {
       // remaining time at the measured rate minus the time already waited: a fresh short
       // job goes first, a job that has waited as long as it still needs overtakes it
@@ -269,16 +291,26 @@ mpc_status run_batched(mpc_server s, double deadline) {
         min_left = std::min(min_left, j->spec.steps - j->h->target_step);
       }
     }
+    Job* const head = s->priority_head ? s->head : nullptr;
+    if (head) min_left = std::min(min_left, head->spec.steps - head->h->target_step);
     const bool launched = min_left != INT64_MAX;
     if (launched) {
       // the next chunk ends where the first resident job finishes (at most chunk steps)
       const int64_t n = std::max<int64_t>(1, std::min<int64_t>(min_left, s->chunk));
       if (cudaEventRecord(s->chunk_start, s->stream) != cudaSuccess)
         return sfail(s, MPC_ECUDA, "event record failed");
-      if (mpc_status st = mpc_batch_step(s->batch, n); st != MPC_OK)
-        return sfail(s, st, std::string("batch step: ") + mpc_batch_last_error(s->batch));
+      if (chunk_work > 0.0)  // (with priority_head the batch may have nothing to step)
+        if (mpc_status st = mpc_batch_step(s->batch, n); st != MPC_OK)
+          return sfail(s, st, std::string("batch step: ") + mpc_batch_last_error(s->batch));
       if (cudaEventRecord(s->chunk_done, s->stream) != cudaSuccess)
         return sfail(s, MPC_ECUDA, "event record failed");
+      if (head) {
+        if (mpc_status st = mpc_step(head->h, n); st != MPC_OK)
+          return sfail(s, st, "head job: " + head->h->err);
+        chunk_work += (double)head->h->N;
+        if (cudaEventRecord(s->head_done, s->head_stream) != cudaSuccess)
+          return sfail(s, MPC_ECUDA, "event record failed");
+      }
       if (s->gap_open) s->stats.host_gap_ms += 1e3 * (now_s(s->t0) - s->gap_from);
       s->stats.chunks += 1;
       s->stats.chunk_steps += n;
@@ -298,7 +330,8 @@ mpc_status run_batched(mpc_server s, double deadline) {
       continue;
     }
     // admit arrivals while the chunk runs; they join the next chunk
-    while (cudaEventQuery(s->chunk_done) == cudaErrorNotReady) {
+    while (cudaEventQuery(s->chunk_done) == cudaErrorNotReady ||
+           (head && cudaEventQuery(s->head_done) == cudaErrorNotReady)) {
       admit(s);
       std::this_thread::sleep_for(std::chrono::microseconds(200));
     }
@@ -314,6 +347,11 @@ mpc_status run_batched(mpc_server s, double deadline) {
       return sfail(s, st, std::string("batch: ") + mpc_batch_last_error(s->batch));
     for (Job& j : s->jobs) {
       if (j.res.status != MPC_JOB_RUNNING || !j.h || j.h->target_step < j.spec.steps) continue;
+      if (&j == s->head) {
+        batch_set_detached(j.h, false);
+        j.h->stream = s->stream;
+        s->head = nullptr;
+      }
       const mpc_status st = fetch(s, j);
       mpc_batch_remove(s->batch, j.h);
       j.h = nullptr;
@@ -367,6 +405,8 @@ mpc_status mpc_server_destroy(mpc_server s) {
   if (s->batch) mpc_batch_destroy(s->batch);
   if (s->chunk_done) cudaEventDestroy(s->chunk_done);
   if (s->chunk_start) cudaEventDestroy(s->chunk_start);
+  if (s->head_done) cudaEventDestroy(s->head_done);
+  if (s->head_stream) cudaStreamDestroy(s->head_stream);
   if (s->side) cudaStreamDestroy(s->side);
   delete s;
   return MPC_OK;
@@ -379,7 +419,7 @@ mpc_status mpc_server_create(const mpc_server_config* cfg, void* stream, mpc_ser
       cfg->max_active > kMaxBatchBoxes || cfg->fill_kparticles < 0 ||
       (cfg->flags & ~(uint32_t)(MPC_SERVER_DETERMINISTIC | MPC_SERVER_SEQUENTIAL |
                                 MPC_SERVER_SHARE_ALL | MPC_SERVER_FIRST_COME | MPC_SERVER_AGED |
-                                MPC_SERVER_BACKFILL)))
+                                MPC_SERVER_BACKFILL | MPC_SERVER_PRIORITY_HEAD)))
     return sfail(nullptr, MPC_EINVAL, "invalid server configuration");
   mpc_server s = new (std::nothrow) mpc_server_s();
   if (!s) return sfail(nullptr, MPC_ENOMEM, "host allocation failed");
@@ -391,6 +431,8 @@ mpc_status mpc_server_create(const mpc_server_config* cfg, void* stream, mpc_ser
   s->first_come = (cfg->flags & MPC_SERVER_FIRST_COME) != 0;
   s->aged = (cfg->flags & MPC_SERVER_AGED) != 0;
   s->backfill = (cfg->flags & MPC_SERVER_BACKFILL) != 0;
+  s->priority_head = (cfg->flags & MPC_SERVER_PRIORITY_HEAD) != 0 &&
+                     (cfg->flags & MPC_SERVER_SEQUENTIAL) == 0;
   if (cfg->fill_kparticles > 0) s->fill = (int64_t)cfg->fill_kparticles * 1000;
   s->chunk = cfg->chunk_steps > 0 ? cfg->chunk_steps : 100;
   if (cudaEventCreate(&s->chunk_done) != cudaSuccess || cudaEventCreate(&s->chunk_start) != cudaSuccess ||
@@ -398,6 +440,16 @@ mpc_status mpc_server_create(const mpc_server_config* cfg, void* stream, mpc_ser
     cudaGetLastError();
     mpc_server_destroy(s);
     return sfail(nullptr, MPC_ECUDA, "event or stream creation failed");
+  }
+  if (s->priority_head) {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&s->head_stream, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->head_done, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      mpc_server_destroy(s);
+      return sfail(nullptr, MPC_ECUDA, "priority stream creation failed");
+    }
   }
   if (!s->sequential) {
     mpc_batch_config bc{};

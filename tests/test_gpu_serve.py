@@ -56,7 +56,8 @@ def _run(mpc, jobs, budget, **kw):
 
 
 @pytest.mark.parametrize("policy", [{}, {"share_all": True}, {"first_come": True},
-                                    {"fill_kparticles": 1}])
+                                    {"fill_kparticles": 1}, {"aged": True, "backfill": True},
+                                    {"priority_head": True}])
 def test_each_job_same_alone_and_in_the_mix(policy):
     mpc = _mpc()
     peaks = [_peak(mpc, j)[1] for j in TRACE]
@@ -76,7 +77,8 @@ def test_each_job_same_alone_and_in_the_mix(policy):
         assert r_one["eta_gk"] == r_mix["eta_gk"]
 
 
-@pytest.mark.parametrize("policy", [{}, {"aged": True}, {"share_all": True}])
+@pytest.mark.parametrize("policy", [{}, {"aged": True}, {"share_all": True},
+                                    {"priority_head": True}])
 def test_each_job_same_alone_and_in_the_mix_float_mode(policy):
     """Float mode (the default: float cell sums, whose order depends on the other boxes of a
     launch): one step of every job of the trace, alone and in the mix, gives bit-identical
