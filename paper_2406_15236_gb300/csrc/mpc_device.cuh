@@ -47,9 +47,39 @@ __device__ __forceinline__ uint4 draw(const Geom& g, uint32_t index, uint32_t st
   return philox4x32(index, step, (tag << 24) | sub, g.box, g.rk);
 }
 
-// (k + 1/2) 2^-23 from the top 23 bits: exact in float32
+// (k + 1/2) 2^-23 from the top 23 bits: k 2^-23 + 2^-24 in one fused operation, exact in
+// float32 (k < 2^23)
 __device__ __forceinline__ float u01(uint32_t r) {
-  return __fmul_rn(__fadd_rn((float)(r >> 9), 0.5f), 1.1920928955078125e-7f);
+  return __fmaf_rn((float)(r >> 9), 1.1920928955078125e-7f, 5.9604644775390625e-8f);
+}
+
+// 2 u01(r) - 1 = (k + 1/2) 2^-22 - 1, exact in float32
+__device__ __forceinline__ float u11(uint32_t r) {
+  return __fmaf_rn((float)(r >> 9), 2.384185791015625e-7f, -0.99999988079071044921875f);
+}
+
+// The hardware approximations (PTX *.approx.ftz): every argument they get here is a
+// normal float32, where they agree with the non-ftz forms without those forms' subnormal
+// handling
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sin_approx(float x) {
+  float y;
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float cos_approx(float x) {
+  float y;
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
 // Box-Muller pair of standard normals
@@ -67,23 +97,23 @@ __device__ __forceinline__ float2 normal2(uint32_t ra, uint32_t rb) {
 __device__ __forceinline__ float minus_2_log_u01(float u) {
   const float t = 1.0f - u;
   const float series = 2.0f * t * (1.0f + t * (0.5f + t * (1.0f / 3.0f)));
-  const float hw = -1.3862943611198906f * __log2f(u);  // -2 ln 2 log2(u)
+  const float hw = -1.3862943611198906f * lg2_approx(u);  // -2 ln 2 log2(u)
   return t < 0.0078125f ? series : hw;
 }
 
-// The three AT+a random-velocity normals from one Philox draw: the Box-Muller pair of
-// (r.x, r.y) and the cosine normal of (r.z, r.w).  The radius is sqrt(-2 ln u) as
-// y rsqrt(y) (y > 0: u < 1), the angle -cos / -sin of pi (2u - 1) in [-pi, pi) by the
-// hardware approximations (absolute error below 6e-7).  A normal is off by less than
-// 6e-6 in the worst case (radius 5.8, u = 2^-24) and ~1e-6 typically.  These values
-// decide no integer.
-__device__ __forceinline__ float3 normal3_at(uint4 r) {
+// The three AT+a random-velocity normals from one Philox draw, times sigma: the
+// Box-Muller pair of (r.x, r.y) and the cosine normal of (r.z, r.w).  The radius is
+// sqrt(-2 ln u) as y rsqrt(y) (y > 0: u < 1), scaled by sigma once, the angle -cos / -sin
+// of pi (2u - 1) in [-pi, pi) by the hardware approximations (absolute error below
+// 6e-7).  A normal is off by less than 6e-6 in the worst case (radius 5.8, u = 2^-24)
+// and ~1e-6 typically.  These values decide no integer.
+__device__ __forceinline__ float3 normal3_at(uint4 r, float sigma) {
   constexpr float kPi = 3.14159265358979f;
   const float y0 = minus_2_log_u01(u01(r.x)), y1 = minus_2_log_u01(u01(r.z));
-  const float R0 = y0 * rsqrtf(y0), R1 = y1 * rsqrtf(y1);
-  float s, c;
-  __sincosf(kPi * (2.0f * u01(r.y) - 1.0f), &s, &c);
-  const float c1 = __cosf(kPi * (2.0f * u01(r.w) - 1.0f));
+  const float R0 = sigma * (y0 * rsqrt_approx(y0)), R1 = sigma * (y1 * rsqrt_approx(y1));
+  const float a0 = kPi * u11(r.y);
+  const float c = cos_approx(a0), s = sin_approx(a0);
+  const float c1 = cos_approx(kPi * u11(r.w));
   return make_float3(-R0 * c, -R0 * s, -R1 * c1);
 }
 

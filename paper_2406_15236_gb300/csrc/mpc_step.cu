@@ -483,6 +483,7 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
   // Stored positions are already streamed for this step (the previous step streamed
   // them when it predicted their brick); the stored velocity is the one they streamed
   // with, before the kick.
+  bool binerr = false;
   for (int i = tid; i < cnt; i += kThreads) {
     const uint32_t zraw = sz[i];
     const uint32_t x = sx[i], y = sy[i], z = zraw & ~kCrossedBit;
@@ -497,26 +498,25 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
       cx = cell_axis(g, x, S0x, 0); cy = cell_axis(g, y, S0y, 1); cz = cell_axis(g, z, S0z, 2);
       lx = cx - ox; ly = cy - oy; lz = cz - oz;
     }
-    uint32_t lcr;
-    if ((unsigned)lx < (unsigned)B0 && (unsigned)ly < (unsigned)B1 &&
-        (unsigned)lz < (unsigned)B2) {
-      const uint32_t lc = (uint32_t)(lx | (ly << Bs0) | (lz << (Bs0 + Bs1)));
-      lcr = lc | (atomicAdd(&scount[lc], 1u) << kCellBits);
-    } else {
-      lcr = kNoCell;  // not binned here: keep the particle, skip its collision
-      atomicOr(&a.ctrl->errors, kErrBinning);
-    }
+    // a particle outside the brick's cells is kept but skips its collision (kNoCell)
+    const bool in = (unsigned)lx < (unsigned)B0 && (unsigned)ly < (unsigned)B1 && (unsigned)lz < (unsigned)B2;
+    const uint32_t lc = in ? (uint32_t)(lx | (ly << Bs0) | (lz << (Bs0 + Bs1))) : 0u;
+    uint32_t rank = 0;
+    if (in) rank = atomicAdd(&scount[lc], 1u);
+    const uint32_t lcr = in ? (lc | (rank << kCellBits)) : kNoCell;
+    binerr |= !in;
     stag[i] = (Tag)lcr;
     if (g.debug) sgc[i] = (uint32_t)cx + (uint32_t)g.Lc[0] * ((uint32_t)cy + (uint32_t)g.Lc[1] * (uint32_t)cz);
     if constexpr (VAR == 1) {
       // AT+a: keep v_ran and w = v - v_ran
-      const float3 n = normal3_at(draw(g, sid[i], step, kTagAtVel, 0u));
-      const float ux = g.sigma * n.x, uy = g.sigma * n.y, uz = g.sigma * n.z;
+      const float3 u = normal3_at(draw(g, sid[i], step, kTagAtVel, 0u), g.sigma);
+      const float ux = u.x, uy = u.y, uz = u.z;
       sux[i] = ux; suy[i] = uy; suz[i] = uz;
       vx -= ux; vy -= uy; vz -= uz;
     }
     svx[i] = vx; svy[i] = vy; svz[i] = vz;
   }
+  if (binerr) atomicOr(&a.ctrl->errors, kErrBinning);
   __syncthreads();
 
   // ---- 3a. offsets of the cells' member lists ----
@@ -697,38 +697,36 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
           r2 = __ll2float_rn(R2) * g.inv2F;
           w0 = from_fx(W0); w1 = from_fx(W1); w2 = from_fx(W2);
         } else {
-          for (int k = sub; k < n; k += tpc) {
-            const int i = sperm[base + k];
-            const float px = rho_axis(g, sx[i], S0x), py = rho_axis(g, sy[i], S0y),
-                        pz = rho_axis(g, sz[i] & ~kCrossedBit, S0z);
-            const float vx = svx[i], vy = svy[i], vz = svz[i];
+          // positions in units of 2^-F (integers, exact in float32): the sums are scaled by
+          // the powers of two at the end, which changes no rounding
+          auto first_term = [&](float px, float py, float pz, float vx, float vy, float vz) {
             r0 += px; r1 += py; r2 += pz;
             w0 += vx; w1 += vy; w2 += vz;
             if constexpr (kOnePass) {
-              o_m[0] += px * px; o_m[1] += py * py; o_m[2] += pz * pz;
-              o_m[3] += px * py; o_m[4] += py * pz; o_m[5] += pz * px;
-              o_m[6] += py * vz - pz * vy; o_m[7] += pz * vx - px * vz; o_m[8] += px * vy - py * vx;
+              o_m[0] = fmaf(px, px, o_m[0]); o_m[1] = fmaf(py, py, o_m[1]); o_m[2] = fmaf(pz, pz, o_m[2]);
+              o_m[3] = fmaf(px, py, o_m[3]); o_m[4] = fmaf(py, pz, o_m[4]); o_m[5] = fmaf(pz, px, o_m[5]);
+              o_m[6] = fmaf(-pz, vy, fmaf(py, vz, o_m[6]));
+              o_m[7] = fmaf(-px, vz, fmaf(pz, vx, o_m[7]));
+              o_m[8] = fmaf(-py, vx, fmaf(px, vy, o_m[8]));
             }
+          };
+          for (int k = sub; k < n; k += tpc) {
+            const int i = sperm[base + k];
+            first_term((float)rho_int(g, sx[i], S0x), (float)rho_int(g, sy[i], S0y),
+                       (float)rho_int(g, sz[i] & ~kCrossedBit, S0z), svx[i], svy[i], svz[i]);
           }
           for (int j = sub; j < nph; j += tpc) {
             const PhantomParticle q = phantom_particle(g, cg, step, j, S0z, pwall);
-            const float px = (float)q.ix * g.inv2F, py = (float)q.iy * g.inv2F,
-                        pz = (float)q.iz * g.inv2F;
-            const float vx = VAR == 1 ? q.vx - q.ux : q.vx, vy = VAR == 1 ? q.vy - q.uy : q.vy,
-                        vz = VAR == 1 ? q.vz - q.uz : q.vz;
-            r0 += px; r1 += py; r2 += pz;
-            w0 += vx; w1 += vy; w2 += vz;
-            if constexpr (kOnePass) {
-              o_m[0] += px * px; o_m[1] += py * py; o_m[2] += pz * pz;
-              o_m[3] += px * py; o_m[4] += py * pz; o_m[5] += pz * px;
-              o_m[6] += py * vz - pz * vy; o_m[7] += pz * vx - px * vz; o_m[8] += px * vy - py * vx;
-            }
+            first_term((float)q.ix, (float)q.iy, (float)q.iz, VAR == 1 ? q.vx - q.ux : q.vx,
+                       VAR == 1 ? q.vy - q.uy : q.vy, VAR == 1 ? q.vz - q.uz : q.vz);
           }
           r0 = group_sum(r0, tpc); r1 = group_sum(r1, tpc); r2 = group_sum(r2, tpc);
           w0 = group_sum(w0, tpc); w1 = group_sum(w1, tpc); w2 = group_sum(w2, tpc);
+          r0 *= g.inv2F; r1 *= g.inv2F; r2 *= g.inv2F;
           if constexpr (kOnePass) {
+            const float s2 = g.inv2F * g.inv2F;
 #pragma unroll
-            for (int q = 0; q < 9; ++q) o_m[q] = group_sum(o_m[q], tpc);
+            for (int q = 0; q < 9; ++q) o_m[q] = group_sum(o_m[q], tpc) * (q < 6 ? s2 : g.inv2F);
           }
         }
         const int nt = n + nph;  // members: fluid and phantom particles
@@ -863,28 +861,28 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
     uint32_t x = sx[i], y = sy[i], z = sz[i] & ~kCrossedBit;
     float vbx = svx[i], vby = svy[i], vbz = svz[i];  // AT+a: w
     const uint32_t lcr = stag[i];
-    const uint32_t lc = lcr == kNoCell ? kNoCell : (lcr & kCellMask);
+    // a particle without a cell (kNoCell) keeps its velocity: computed with cell 0's
+    // parameters and discarded, so the common path has no branch
+    const bool has = lcr != kNoCell;
+    const uint32_t lc = has ? (lcr & kCellMask) : 0u;
+    const float* P = spar + lc;
     float nx, ny, nz;
     // positions relative to the collision-cell centre (collisional stress, AT+a omega x r)
     const float px = rho_axis(g, x, S0x), py = rho_axis(g, y, S0y), pz = rho_axis(g, z, S0z);
     if constexpr (VAR == 0) {
-      nx = vbx; ny = vby; nz = vbz;
-      if (lc != kNoCell) {
-        const float* P = spar + lc;
-        const float vcx = P[0], vcy = P[bc], vcz = P[2 * bc];
-        const float ax = P[3 * bc], ay = P[4 * bc], az = P[5 * bc], kap = P[6 * bc];
-        const float rx = vbx - vcx, ry = vby - vcy, rz = vbz - vcz;
-        const float nr = ax * rx + ay * ry + az * rz;
-        const float t = (1.0f - g.cos_a) * nr;
-        nx = vcx + kap * (g.cos_a * rx + g.sin_a * (ay * rz - az * ry) + t * ax);
-        ny = vcy + kap * (g.cos_a * ry + g.sin_a * (az * rx - ax * rz) + t * ay);
-        nz = vcz + kap * (g.cos_a * rz + g.sin_a * (ax * ry - ay * rx) + t * az);
-      }
+      const float vcx = P[0], vcy = P[bc], vcz = P[2 * bc];
+      const float ax = P[3 * bc], ay = P[4 * bc], az = P[5 * bc], kap = P[6 * bc];
+      const float rx = vbx - vcx, ry = vby - vcy, rz = vbz - vcz;
+      const float nr = ax * rx + ay * ry + az * rz;
+      const float t = (1.0f - g.cos_a) * nr;
+      nx = vcx + kap * (g.cos_a * rx + g.sin_a * (ay * rz - az * ry) + t * ax);
+      ny = vcy + kap * (g.cos_a * ry + g.sin_a * (az * rx - ax * rz) + t * ay);
+      nz = vcz + kap * (g.cos_a * rz + g.sin_a * (ax * ry - ay * rx) + t * az);
+      nx = has ? nx : vbx; ny = has ? ny : vby; nz = has ? nz : vbz;
     } else if constexpr (VAR == 2) {
       // SRD+a, Eq. (3): v' = v_cm + D v_ic + omega x r_ic
       nx = vbx; ny = vby; nz = vbz;
-      if (lc != kNoCell) {
-        const float* P = spar + lc;
+      if (has) {
         const float vcx = P[0], vcy = P[bc], vcz = P[2 * bc];
         const float wx = P[3 * bc], wy = P[4 * bc], wz = P[5 * bc];
         const float rx = px - P[6 * bc], ry = py - P[7 * bc], rz = pz - P[8 * bc];
@@ -899,14 +897,11 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
     } else {
       const float ux = sux[i], uy = suy[i], uz = suz[i];
       vbx += ux; vby += uy; vbz += uz;  // the velocity the particle streamed with
-      nx = vbx; ny = vby; nz = vbz;
-      if (lc != kNoCell) {
-        const float* P = spar + lc;
-        const float wx = P[3 * bc], wy = P[4 * bc], wz = P[5 * bc];
-        nx = P[0] + ux + (wy * pz - wz * py);
-        ny = P[bc] + uy + (wz * px - wx * pz);
-        nz = P[2 * bc] + uz + (wx * py - wy * px);
-      }
+      const float wx = P[3 * bc], wy = P[4 * bc], wz = P[5 * bc];
+      nx = P[0] + ux + (wy * pz - wz * py);
+      ny = P[bc] + uy + (wz * px - wx * pz);
+      nz = P[2 * bc] + uz + (wx * py - wy * px);
+      nx = has ? nx : vbx; ny = has ? ny : vby; nz = has ? nz : vbz;
     }
     if (g.obs) {
       if constexpr (DET) {
@@ -917,7 +912,7 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
         for (int q = 0; q < 13; ++q) o_q[q] += fixed_of<24>(t[q]);
       } else {
         o_px += nx; o_py += ny; o_pz += nz;
-        o_e += nx * nx + ny * ny + nz * nz;
+        o_e = fmaf(nz, nz, fmaf(ny, ny, fmaf(nx, nx, o_e)));
         o_kxy += vbx * vby; o_kyz += vby * vbz; o_kzx += vbz * vbx;
         const float dx = nx - vbx, dy = ny - vby, dz = nz - vbz;
         o_c[0] += dx * py; o_c[1] += dy * px; o_c[2] += dy * pz;
@@ -949,21 +944,15 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
                  ? 27u
                  : (uint32_t)((dxb + 1) + 3 * (dyb + 1) + 9 * (dzb + 1));
     }
-    // rank within the destination group: particles that stay in this brick (most of
-    // them) get consecutive slots through one warp ballot, so their writes below are
-    // contiguous runs; the others take a shared-memory atomic each
+    // rank within the destination group: the lanes of a warp bound for the same group
+    // (most of them stay in this brick) get consecutive slots from one shared-memory
+    // atomic by the first of them, so their writes below are contiguous runs
     const uint32_t active = __activemask();
-    const uint32_t stay = __ballot_sync(active, code == 13u);
-    uint32_t rank;
-    if (code == 13u) {
-      const int first = __ffs(stay) - 1;
-      uint32_t rank0 = 0;
-      if (lane == first) rank0 = atomicAdd(&gcount[13], (uint32_t)__popc(stay));
-      rank0 = __shfl_sync(stay, rank0, first);
-      rank = rank0 + (uint32_t)__popc(stay & ((1u << lane) - 1u));
-    } else {
-      rank = atomicAdd(&gcount[code], 1u);
-    }
+    const uint32_t peers = __match_any_sync(active, code);
+    const int leader = __ffs(peers) - 1;
+    uint32_t rank0 = 0;
+    if (lane == leader) rank0 = atomicAdd(&gcount[code], (uint32_t)__popc(peers));
+    const uint32_t rank = __shfl_sync(active, rank0, leader) + (uint32_t)__popc(peers & ((1u << lane) - 1u));
     stag[i] = (Tag)(code | (rank << 5));
   }
   if (g.obs) {
@@ -1028,9 +1017,35 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
   }
 
   // ---- 6. write out: each particle to its reserved slot ----
+  // The destination arrays of this step's parity, held in registers for the loop
+  uint32_t* const dX = par ? a.buf[0].x[0] : a.buf[1].x[0];
+  uint32_t* const dY = par ? a.buf[0].x[1] : a.buf[1].x[1];
+  uint32_t* const dZ = par ? a.buf[0].x[2] : a.buf[1].x[2];
+  float* const dVX = par ? a.buf[0].v[0] : a.buf[1].v[0];
+  float* const dVY = par ? a.buf[0].v[1] : a.buf[1].v[1];
+  float* const dVZ = par ? a.buf[0].v[2] : a.buf[1].v[2];
+  uint32_t* const dID = par ? a.buf[0].id : a.buf[1].id;
+  bool rare = false;
   for (int i = tid; i < cnt; i += kThreads) {
     const uint32_t t = stag[i];
     const uint32_t code = t & 31u;
+    const uint32_t slot = gbase[code] + (t >> 5);  // meaningless for code 27, not used
+    if (code < 27 && slot < (uint32_t)cap) {
+      const size_t o = (size_t)gdest[code] * cap + slot;
+      dX[o] = sx[i]; dY[o] = sy[i]; dZ[o] = sz[i];
+      dVX[o] = svx[i]; dVY[o] = svy[i]; dVZ[o] = svz[i];
+      dID[o] = sid[i];
+      if (g.debug) dst.cell[o] = sgc[i];
+    } else {
+      rare = true;
+    }
+  }
+  // the rare ones, kept out of the loop above: a particle bound beyond the neighbour
+  // bricks (a global atomic for its slot) or past its destination's capacity (spilled)
+  for (int i = tid; rare && i < cnt; i += kThreads) {
+    const uint32_t t = stag[i];
+    const uint32_t code = t & 31u;
+    if (code < 27 && gbase[code] + (t >> 5) < (uint32_t)cap) continue;
     uint32_t d, slot;
     if (code < 27) {
       d = gdest[code];
@@ -1044,9 +1059,9 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
     }
     if (slot < (uint32_t)cap) {
       const size_t o = (size_t)d * cap + slot;
-      dst.x[0][o] = sx[i]; dst.x[1][o] = sy[i]; dst.x[2][o] = sz[i];
-      dst.v[0][o] = svx[i]; dst.v[1][o] = svy[i]; dst.v[2][o] = svz[i];
-      dst.id[o] = sid[i];
+      dX[o] = sx[i]; dY[o] = sy[i]; dZ[o] = sz[i];
+      dVX[o] = svx[i]; dVY[o] = svy[i]; dVZ[o] = svz[i];
+      dID[o] = sid[i];
       if (g.debug) dst.cell[o] = sgc[i];
     } else {
       atomicExch(&a.ctrl->overflow, 1);
