@@ -33,7 +33,7 @@ METRIC = "MPC particle-steps/s at 512³·N_c=10, % HBM roofline; batched jobs/s,
 UNIT = "particle-steps/s"
 BYTES_PER_PARTICLE = 56  # fused step: read + write of x,y,z (u32), vx,vy,vz (f32), id (u32)
 TWO_SWEEP_MODEL_BYTES = 72  # the two-sweep lower bound of the conventional design
-KERNEL_SOURCES = ["paper_2406_15236_gb300/csrc/mpc_step.cu",
+KERNEL_SOURCES = ["paper_2406_15236_gb300/csrc/mpc_step.cuh",
                   "paper_2406_15236_gb300/csrc/mpc_device.cuh",
                   "paper_2406_15236_gb300/csrc/mpc_internal.h"]
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_step_at_a.md")

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libmpc_gb300.so")
-SOURCES = ["mpc_step.cu", "mpc_layout.cu", "mpc_api.cu", "mpc_batch.cu", "mpc_serve.cu", "mpc_checkpoint.cu", "mpc_noalloc.cu"]
+SOURCES = ["mpc_step_at_a.cu", "mpc_step_srd.cu", "mpc_step_srd_a.cu", "mpc_step.cu", "mpc_layout.cu", "mpc_api.cu", "mpc_batch.cu", "mpc_serve.cu", "mpc_checkpoint.cu", "mpc_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -174,6 +174,7 @@ StepArgs step_args(mpc_handle h) {
   a.obs_series = h->obs_series;
   a.obs_ring = h->obs_ring;
   a.dbg_counts = h->dbg_counts;
+  a.deferred = h->deferred;
   return a;
 }
 
@@ -515,6 +516,7 @@ void box_footprint(const Geom& g, int64_t N, size_t& steady, size_t& peak) {
   s += 8 * rounded(sp * 4) + (g.debug ? rounded(sp * 4) : 0);  // x, v, id, dest (+ cell)
   s += rounded(sizeof(double) * kObsSlots * kObsWidth);
   if (g.debug) s += rounded((size_t)g.ncells * 4);
+  s += rounded(((size_t)g.nbricks + 2) * 4);  // deferred bricks
   s += 2 * (7 + (g.debug ? 1 : 0)) * rounded(n * 4);
   steady = s;
   // creation: contiguous staging (7 arrays) + init sums + bin counts
@@ -581,6 +583,9 @@ mpc_status create_box(const mpc_params* p, cudaStream_t stream, const mpc_alloca
   if ((st = alloc_array(h, &h->obs_partials, (size_t)kObsSlots * kObsWidth, "observables")) != MPC_OK) return bail(st);
   if ((st = alloc_array(h, &h->obs_series, (size_t)h->obs_ring * kObsWidth, "observables")) != MPC_OK) return bail(st);
   if (g.debug && (st = alloc_array(h, &h->dbg_counts, (size_t)g.ncells, "debug counts")) != MPC_OK) return bail(st);
+  if ((st = alloc_array(h, &h->deferred, (size_t)g.nbricks + 2, "deferred bricks")) != MPC_OK) return bail(st);
+  if (cudaMemsetAsync(h->deferred, 0, ((size_t)g.nbricks + 2) * 4, h->stream) != cudaSuccess)
+    return bail(fail(h, MPC_ECUDA, "memset"));
   if ((st = alloc_particle_buffers(h)) != MPC_OK) return bail(st);
   if (configure_step_kernels(h->smem_limit) != cudaSuccess)
     return bail(fail(h, MPC_ECUDA, "cannot configure the step kernel (shared memory)"));

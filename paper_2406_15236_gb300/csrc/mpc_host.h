@@ -31,6 +31,7 @@ struct mpc_s {
   double* obs_series = nullptr;
   int obs_ring = 1024;
   uint32_t* dbg_counts = nullptr;
+  uint32_t* deferred = nullptr;    // bricks deferred to the full-capacity pass
   int64_t target_step = 0;
   int64_t limit = INT64_MAX;       // the box stops advancing at this step
   cudaGraphExec_t graph = nullptr;

@@ -86,6 +86,11 @@ struct StepArgs {
   double* obs_series;     // ring * kObsWidth
   int obs_ring;
   uint32_t* dbg_counts;   // ncells (debug)
+  // bricks left to the full-capacity pass of a step (their particles did not fit the
+  // smaller shared-memory tile of the kernel that runs more CTAs per SM): word 0 counts
+  // them, word 1 counts the CTAs of that pass that finished, words 2.. hold brick indices
+  // (nbricks + 2 words, zero between steps)
+  uint32_t* deferred;
 };
 
 // Step arguments of every member of a batch (device memory), for the kernel that

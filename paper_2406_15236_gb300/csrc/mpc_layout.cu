@@ -123,7 +123,7 @@ __global__ void k_bin_scatter(const Geom g, int64_t N, const uint32_t* x0, const
     atomicOr(errors, kErrRange);
     return;
   }
-  // bricks hold positions already streamed for the coming step (see mpc_step.cu)
+  // bricks hold positions already streamed for the coming step (see mpc_step.cuh)
   const size_t o = (size_t)b * g.cap + slot;
   dst.x[0][o] = x; dst.x[1][o] = y; dst.x[2][o] = z;
   dst.v[0][o] = v0[i]; dst.v[1][o] = v1[i]; dst.v[2][o] = v2[i];

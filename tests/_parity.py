@@ -136,3 +136,23 @@ def check_step(p_oracle, pre, post, step, kT=1.0, m=1.0, post_cells=None, gpu_co
                                        f"exceeds its bar (ratio {stats['max_ratio']:.3g})")
     stats["ref"] = ref
     return stats
+
+
+def check_subset(ref, X1, V1, keep, kT=1.0, m=1.0, strict_flags=oracle.FLAG_DEGENERATE, what=""):
+    """Compare the GPU result (X1, V1: the same particles as the oracle's `ref`, in its
+    order) on the particles selected by `keep` -- the members of cells whose every member
+    took part in the oracle step -- with the bar of check_step.  Returns the largest
+    velocity error outside ill-conditioned cells."""
+    np.testing.assert_array_equal(X1[:, keep], ref["X"][:, keep], err_msg=f"{what}: positions differ")
+    vref = ref["V"][:, keep]
+    scale = np.maximum(np.linalg.norm(vref, axis=0), np.sqrt(kT / m))
+    err = np.linalg.norm(V1[:, keep].astype(np.float64) - vref, axis=0) / scale
+    cflags = ref["flags"][ref["cell"][keep]]
+    skip = (cflags & strict_flags) != 0
+    illc = (cflags & oracle.FLAG_ILL_CONDITIONED) != 0
+    bar = np.where(illc, np.maximum(VEL_TOL, SENS_FACTOR * ULP32 * ref["sens"][keep] / scale), VEL_TOL)
+    bad = (err > bar) & ~skip
+    assert not bad.any(), (f"{what}: {bad.sum()} velocities above their bar, worst "
+                           f"{float(err[bad].max()):.3g} (ill-conditioned: {int((bad & illc).sum())})")
+    strict = ~skip & ~illc
+    return float(err[strict].max()) if strict.any() else 0.0

@@ -1,0 +1,93 @@
+"""The deferring step kernel of large MPC-AT+a boxes.
+
+Boxes of 8192 bricks or more step with a kernel whose shared-memory tile holds 736 of a
+brick's 864 slots (7 CTAs per SM instead of 6); a brick that holds more particles in a
+step is left to a full-capacity pass launched right after it.  At uniform density that
+is ~7e-5 of the bricks.  Here a 128^3 box (32,768 bricks of 4^3 cells) gets a denser slab
+(N_c 11.5 in x < 32, so about half of that slab's bricks exceed the tile) by moving
+particles into it with set_state.  For two consecutive steps, particles of cells sampled
+inside the slab and outside it are compared with the oracle (stepped on the neighbourhood
+of each sampled cell: the particles that collide in cell c come from unshifted cells
+c-2..c+1 per axis); the second step also shows that the list of deferred bricks was
+cleared in between.  The whole particle set (count, ids) must survive.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from tests import _parity as par
+
+pytestmark = pytest.mark.gpu
+
+L = 128
+KW = dict(L=L, n_c=10.0, h=0.05, kT=1.0, variant=1, seed=11)
+
+
+def _dense_slab_state(X, F, rng):
+    """moves 7.5 % of the particles of x >= L/2 to uniform positions in x < L/4: the
+    slab's density becomes 10 (1 + 0.075 * 2) = 11.5 per cell"""
+    src = np.nonzero((X[0] >> F) >= L // 2)[0]
+    pick = rng.choice(src, size=int(0.075 * src.size), replace=False)
+    X = X.copy()
+    X[0, pick] = rng.integers(0, (L // 4) << F, size=pick.size, dtype=np.uint64).astype(np.uint32)
+    return X
+
+
+def _neighbourhood(X, F, cells):
+    ucell = (X[0] >> F).astype(np.int64) + L * ((X[1] >> F).astype(np.int64) + L * (X[2] >> F).astype(np.int64))
+    mark = np.zeros(L ** 3, dtype=bool)
+    offs = np.arange(-2, 2)
+    for cx, cy, cz in cells:
+        gx, gy, gz = np.meshgrid((cx + offs) % L, (cy + offs) % L, (cz + offs) % L, indexing="ij")
+        mark[(gx + L * (gy + L * gz)).ravel()] = True
+    return mark[ucell]
+
+
+def test_deferred_bricks_match_oracle():
+    import torch
+
+    import paper_2406_15236_gb300 as mpc
+
+    torch.cuda.set_device(0)
+    sim = mpc.Simulation(flags=mpc.MPC_FLAG_OBSERVABLES, **KW)
+    N = sim.N
+    F = sim.info.fixed_bits
+    nb = sim.info.n_bricks
+    assert nb[0] * nb[1] * nb[2] >= 8192
+    rng = np.random.default_rng(5)
+    X, V, ids, s = sim.get_state()
+    X = _dense_slab_state(X, F, rng)
+    sim.set_state(X, V, ids, s)
+    # cells inside the dense slab (most of them in deferred bricks) and outside it
+    cells = np.concatenate([
+        np.stack([rng.integers(2, L // 4 - 2, 40), rng.integers(0, L, 40), rng.integers(0, L, 40)], axis=1),
+        np.stack([rng.integers(L // 2, L, 10), rng.integers(0, L, 10), rng.integers(0, L, 10)], axis=1)])
+    sampled = set(int(cx + L * (cy + L * cz)) for cx, cy, cz in cells)
+    p = par.oracle_params(**KW)
+    for k in range(2):
+        X0, V0, id0, s0 = sim.get_state()
+        assert X0.shape[1] == N and int(id0.astype(np.int64).sum()) == N * (N - 1) // 2
+        sel = _neighbourhood(X0, F, cells)
+        Xs, Vs, idss = X0[:, sel], V0[:, sel], id0[sel]
+        sim.step(1)
+        X1, V1, id1, s1 = sim.get_state()
+        assert s1 == s0 + 1
+        assert int(id1.astype(np.int64).sum()) == N * (N - 1) // 2
+        idm = np.zeros(N, dtype=bool)
+        idm[idss] = True
+        sel1 = idm[id1]
+        o0 = np.argsort(idss)
+        o1 = np.argsort(id1[sel1])
+        assert np.array_equal(id1[sel1][o1], idss[o0])
+        ref = oracle.step(p, Xs[:, o0], Vs[:, o0].astype(np.float64), idss[o0], s0, cells=True,
+                          sens=True, flags=True)
+        keep = np.array([c in sampled for c in ref["cell"]])
+        in_slab = keep & ((ref["X"][0] >> F) < L // 4)
+        assert keep.sum() > 400 and in_slab.sum() > 300
+        worst = par.check_subset(ref, X1[:, sel1][:, o1], V1[:, sel1][:, o1], keep,
+                                 what=f"step {s0}")
+        print(f"step {s0}: {keep.sum()} particles of {len(sampled)} sampled cells "
+              f"({in_slab.sum()} in the dense slab), max velocity error {worst:.3g}")
+    info = mpc.mpc_get_info(sim.handle)
+    assert info.recoveries == 0  # no brick overflowed: the deferral, not the repair, ran
+    sim.close()

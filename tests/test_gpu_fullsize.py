@@ -101,13 +101,6 @@ def test_fullsize_sampled_cells_match_oracle():
     # the collision cell index on the shifted lattice equals cx + L(cy + L cz) for periodic boxes
     keep = np.array([c in sampled for c in ref["cell"]])
     assert keep.sum() > 300
-    Xg, Vg = X1[:, o1][:, keep], V1[:, o1][:, keep]
-    np.testing.assert_array_equal(Xg, ref["X"][:, keep])
-    vref = ref["V"][:, keep]
-    scale = np.maximum(np.linalg.norm(vref, axis=0), 1.0)
-    err = np.linalg.norm(Vg.astype(np.float64) - vref, axis=0) / scale
-    bar = np.maximum(par.VEL_TOL, 16 * par.ULP32 * ref["sens"][keep] / scale)
-    degenerate = (ref["flags"][ref["cell"][keep]] & oracle.FLAG_DEGENERATE) != 0
-    assert np.all(err[~degenerate] <= bar[~degenerate]), float(err.max())
+    worst = par.check_subset(ref, X1[:, o1], V1[:, o1], keep, what="full size")
     print(f"full size: {keep.sum()} particles in {len(sampled)} sampled cells, "
-          f"max velocity error {err.max():.3g}")
+          f"max velocity error outside ill-conditioned cells {worst:.3g}")
