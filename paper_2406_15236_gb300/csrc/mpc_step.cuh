@@ -966,10 +966,26 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
     const uint32_t rank = __shfl_sync(active, rank0, leader) + (uint32_t)__popc(peers & ((1u << lane) - 1u));
     stag[i] = (Tag)(code | (rank << 5));
   }
-  // ---- 5. per warp: observables partials, this warp's runs in the destination bricks
-  // (one global atomic per destination group of the warp), and the write-out of the
-  // warp's own particles -- the ones it collided, so no block barrier is needed ----
+  // ---- 5. per warp: this warp's runs in the destination bricks (one global atomic per
+  // destination group of the warp, issued first so that its round trip overlaps the
+  // observables reduction), the observables partials, and the write-out of the warp's
+  // own particles -- the ones it collided, so no block barrier is needed ----
   const int w = tid >> 5;
+  __syncwarp();
+  uint32_t rbase = 0, rdest = 0;  // lane c: the warp's run for destination code c
+  if (lane < 27) {
+    const uint32_t n = wcount[28 * w + lane];
+    if (n > 0) {
+      const int dxb = lane % 3 - 1, dyb = (lane / 3) % 3 - 1, dzb = lane / 9 - 1;
+      int qx = bx + dxb, qy = by + dyb, qz = bz + dzb;
+      if (qx < 0) qx += g.nb[0]; else if (qx >= g.nb[0]) qx -= g.nb[0];
+      if (qy < 0) qy += g.nb[1]; else if (qy >= g.nb[1]) qy -= g.nb[1];
+      if (zper) { if (qz < 0) qz += g.nb[2]; else if (qz >= g.nb[2]) qz -= g.nb[2]; }
+      rdest = (uint32_t)(qx + g.nb[0] * (qy + g.nb[1] * qz));
+      rbase = atomicAdd(&cnt_dst[rdest], n);
+    }
+  }
+
   if (g.obs) {
     double* orow = &a.obs_partials[(b % kObsSlots) * kObsWidth];
     if constexpr (DET) {
@@ -986,21 +1002,6 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
       if (!(lane & 1) && (lane >> 1) < 13) atomicAdd(orow + (lane >> 1), (double)s);
     }
   }
-  __syncwarp();
-  uint32_t rbase = 0, rdest = 0;  // lane c: the warp's run for destination code c
-  if (lane < 27) {
-    const uint32_t n = wcount[28 * w + lane];
-    if (n > 0) {
-      const int dxb = lane % 3 - 1, dyb = (lane / 3) % 3 - 1, dzb = lane / 9 - 1;
-      int qx = bx + dxb, qy = by + dyb, qz = bz + dzb;
-      if (qx < 0) qx += g.nb[0]; else if (qx >= g.nb[0]) qx -= g.nb[0];
-      if (qy < 0) qy += g.nb[1]; else if (qy >= g.nb[1]) qy -= g.nb[1];
-      if (zper) { if (qz < 0) qz += g.nb[2]; else if (qz >= g.nb[2]) qz -= g.nb[2]; }
-      rdest = (uint32_t)(qx + g.nb[0] * (qy + g.nb[1] * qz));
-      rbase = atomicAdd(&cnt_dst[rdest], n);
-    }
-  }
-
   // ---- 6. write out: each particle to its reserved slot; the ids come from the source
   // brick in global memory (L2: loaded or prefetched with the brick) ----
   uint32_t* const dX = par ? a.buf[0].x[0] : a.buf[1].x[0];
