@@ -1187,7 +1187,7 @@ template <int VAR, bool DET>
 cudaError_t set_cap_tiers(int v) {
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e = cudaFuncSetAttribute(k_step<VAR, DET, 0>, a, v);
-  if constexpr (VAR == 1 && !DET) {
+  if constexpr (VAR == 1) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<VAR, DET, 1, true>, a, v);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<VAR, DET, 2, true>, a, v);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step_deferred<VAR, DET>, a, v);
@@ -1217,7 +1217,7 @@ size_t deferred_smem_bytes(const Geom& g) {
 template <int VAR, bool DET>
 void launch_tier(const StepArgs& a, size_t bytes, cudaStream_t s) {
   const int tier = tier_of(a.g);
-  if constexpr (VAR == 1 && !DET) {
+  if constexpr (VAR == 1) {
     // tiers 1 and 2 (16-bit tags) fit 7 CTAs per SM with the smaller tile; tier 3's 128
     // cells do not
     if ((tier == 1 || tier == 2) && a.g.nbricks >= kDeferMinBricks && a.deferred) {

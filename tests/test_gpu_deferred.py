@@ -9,7 +9,10 @@ particles into it with set_state.  For two consecutive steps, particles of cells
 inside the slab and outside it are compared with the oracle (stepped on the neighbourhood
 of each sampled cell: the particles that collide in cell c come from unshifted cells
 c-2..c+1 per axis); the second step also shows that the list of deferred bricks was
-cleared in between.  The whole particle set (count, ids) must survive.
+cleared in between.  The whole particle set (count, ids) must survive.  In the
+fixed-point mode, where a trajectory does not depend on which kernel processes a brick,
+the same dense-slab box stepped with the deferring kernel and with bricks of 320
+particles (the generic kernel, full tile) must stay bit-identical.
 """
 import numpy as np
 import pytest
@@ -91,3 +94,35 @@ def test_deferred_bricks_match_oracle():
     info = mpc.mpc_get_info(sim.handle)
     assert info.recoveries == 0  # no brick overflowed: the deferral, not the repair, ran
     sim.close()
+
+
+def test_deterministic_deferred_equals_full_tile():
+    import torch
+
+    import paper_2406_15236_gb300 as mpc
+
+    torch.cuda.set_device(0)
+    flags = mpc.MPC_FLAG_DETERMINISTIC | mpc.MPC_FLAG_OBSERVABLES
+    rng = np.random.default_rng(6)
+    results = []
+    state0 = None
+    for tile in (640, 320):
+        sim = mpc.Simulation(flags=flags, tile_particles=tile, **KW)
+        nb = sim.info.n_bricks
+        if tile == 640:
+            assert nb[0] * nb[1] * nb[2] >= 8192 and sim.info.capacity == 864  # deferring kernel
+            X, V, ids, s = sim.get_state()
+            state0 = (_dense_slab_state(X, sim.info.fixed_bits, rng), V, ids, s)
+        else:
+            assert sim.info.capacity != 864  # the generic kernel
+        sim.set_state(*state0)
+        sim.step(6)
+        X, V, ids, s = sim.get_state()
+        o = np.argsort(ids)
+        results.append((X[:, o], V[:, o], s, sim.observable_series(6)))
+        assert mpc.mpc_get_info(sim.handle).recoveries == 0
+        sim.close()
+    assert results[0][2] == results[1][2] == 6
+    assert np.array_equal(results[0][0], results[1][0])
+    assert np.array_equal(results[0][1].view(np.uint32), results[1][1].view(np.uint32))
+    assert np.array_equal(results[0][3], results[1][3])
