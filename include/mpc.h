@@ -367,9 +367,10 @@ enum {
                                      chunk, beyond the fill: small jobs progress beside a
                                      large one at little cost to it */
   MPC_SERVER_PRIORITY_HEAD = 64u  /* the oldest resident job steps on its own stream of the
-                                     highest priority, outside the batch: the GPU's block
-                                     scheduler serves its launches first and the other jobs
-                                     use what it leaves (the stepping order applies to them) */
+                                     highest priority, outside the batch, all its remaining
+                                     steps enqueued at once: the GPU's block scheduler serves
+                                     its launches first and the other jobs use what it leaves
+                                     (the stepping order applies to them) */
 };
 /* By default a chunk steps the resident jobs with the least remaining work (steps x
  * particles) until they hold fill_kparticles thousand particles (default 16M: enough

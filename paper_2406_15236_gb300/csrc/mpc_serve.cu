@@ -57,8 +57,9 @@ struct mpc_server_s {
   cudaStream_t side = nullptr;  // result copies that must not wait for queued chunks
   bool det = false, sequential = false, share_all = false, first_come = false, aged = false,
        backfill = false, priority_head = false;
-  cudaStream_t head_stream = nullptr;  // priority_head: the oldest job's own steps
+  cudaStream_t head_stream = nullptr;  // priority_head: the head job's own steps
   cudaEvent_t head_done = nullptr;
+  cudaEvent_t head_ready = nullptr;  // the batch stream's creations, before the head steps
   Job* head = nullptr;
   double work_done = 0.0;  // particle-steps of the chunks run so far (aged ordering)
   int64_t fill = kFillParticles;
@@ -222,6 +223,32 @@ bool all_finished(const mpc_server s) {
   return true;
 }
 
+// The head job (MPC_SERVER_PRIORITY_HEAD): detached from the batch, all its remaining
+// steps enqueued at once on the high-priority stream, so it runs at its own pace between
+// the batch's chunks instead of pausing at each chunk boundary.
+mpc_status start_head(mpc_server s, Job* j) {
+  s->head = j;
+  // the batch stream waits for member creations; no chunk is pending when a head starts
+  if (cudaEventRecord(s->head_ready, s->stream) != cudaSuccess ||
+      cudaStreamWaitEvent(s->head_stream, s->head_ready, 0) != cudaSuccess)
+    return sfail(s, MPC_ECUDA, "event record failed");
+  j->h->stream = s->head_stream;
+  batch_set_detached(j->h, true);
+  if (mpc_status st = mpc_set_step_limit(j->h, j->spec.steps); st != MPC_OK)
+    return sfail(s, st, "step limit: " + j->h->err);
+  const int64_t n = j->spec.steps - j->h->target_step;
+  if (mpc_status st = mpc_step(j->h, n); st != MPC_OK) return sfail(s, st, "head job: " + j->h->err);
+  if (cudaEventRecord(s->head_done, s->head_stream) != cudaSuccess)
+    return sfail(s, MPC_ECUDA, "event record failed");
+  s->work_done += (double)n * (double)j->h->N;
+  return MPC_OK;
+}
+
+// particle-steps per second of the runs so far (the order keys' time scale)
+double work_rate(const mpc_server s) {
+  return s->stats.gpu_ms > 0.0 ? s->work_done / (1e-3 * s->stats.gpu_ms) : 4e10;
+}
+
 mpc_status run_batched(mpc_server s, double deadline) {
   std::vector<Job*> fetched;  // results on the host, analysis pending
   for (;;) {
@@ -236,30 +263,16 @@ mpc_status run_batched(mpc_server s, double deadline) {
     // at their step
     std::vector<Job*> resident;  // (retired jobs await analysis with h = NULL)
     for (Job& j : s->jobs)
-      if (j.res.status == MPC_JOB_RUNNING && j.h) resident.push_back(&j);
-    if (s->priority_head) {
-      // the oldest resident job steps on its own high-priority stream, outside the batch's
-      // launches: the GPU's block scheduler serves it first, the batch fills what it leaves
-      Job* oldest = resident.empty() ? nullptr : resident.front();  // arrival order
-      if (oldest != s->head) {
-        if (s->head && s->head->h) {
-          batch_set_detached(s->head->h, false);
-          s->head->h->stream = s->stream;
-        }
-        s->head = oldest;
-        if (oldest) {
-          oldest->h->stream = s->head_stream;
-          batch_set_detached(oldest->h, true);
-          if (mpc_status st = mpc_set_step_limit(oldest->h, oldest->spec.steps); st != MPC_OK)
-            return sfail(s, st, "step limit: " + oldest->h->err);
-        }
-      }
-      if (oldest) resident.erase(resident.begin());
+      if (j.res.status == MPC_JOB_RUNNING && j.h && &j != s->head) resident.push_back(&j);
+    if (s->priority_head && !s->head && !resident.empty()) {
+      // the oldest resident job (jobs are kept in arrival order) becomes the head
+      TRY(start_head(s, resident.front()));
+      resident.erase(resident.begin());
     }
     if (s->aged) {
       // remaining time at the measured rate minus the time already waited: a fresh short
       // job goes first, a job that has waited as long as it still needs overtakes it
-      const double rate = s->stats.gpu_ms > 0.0 ? s->work_done / (1e-3 * s->stats.gpu_ms) : 4e10;
+      const double rate = work_rate(s);
       const double t = now_s(s->t0);
       auto key = [&](const Job* j) {
         return (double)(j->spec.steps - j->h->target_step) * (double)j->h->N / rate -
@@ -291,26 +304,17 @@ mpc_status run_batched(mpc_server s, double deadline) {
         min_left = std::min(min_left, j->spec.steps - j->h->target_step);
       }
     }
-    Job* const head = s->priority_head ? s->head : nullptr;
-    if (head) min_left = std::min(min_left, head->spec.steps - head->h->target_step);
+    Job* const head = s->head;
     const bool launched = min_left != INT64_MAX;
     if (launched) {
-      // the next chunk ends where the first resident job finishes (at most chunk steps)
+      // the next chunk ends where the first stepping job finishes (at most chunk steps)
       const int64_t n = std::max<int64_t>(1, std::min<int64_t>(min_left, s->chunk));
       if (cudaEventRecord(s->chunk_start, s->stream) != cudaSuccess)
         return sfail(s, MPC_ECUDA, "event record failed");
-      if (chunk_work > 0.0)  // (with priority_head the batch may have nothing to step)
-        if (mpc_status st = mpc_batch_step(s->batch, n); st != MPC_OK)
-          return sfail(s, st, std::string("batch step: ") + mpc_batch_last_error(s->batch));
+      if (mpc_status st = mpc_batch_step(s->batch, n); st != MPC_OK)
+        return sfail(s, st, std::string("batch step: ") + mpc_batch_last_error(s->batch));
       if (cudaEventRecord(s->chunk_done, s->stream) != cudaSuccess)
         return sfail(s, MPC_ECUDA, "event record failed");
-      if (head) {
-        if (mpc_status st = mpc_step(head->h, n); st != MPC_OK)
-          return sfail(s, st, "head job: " + head->h->err);
-        chunk_work += (double)head->h->N;
-        if (cudaEventRecord(s->head_done, s->head_stream) != cudaSuccess)
-          return sfail(s, MPC_ECUDA, "event record failed");
-      }
       if (s->gap_open) s->stats.host_gap_ms += 1e3 * (now_s(s->t0) - s->gap_from);
       s->stats.chunks += 1;
       s->stats.chunk_steps += n;
@@ -319,7 +323,8 @@ mpc_status run_batched(mpc_server s, double deadline) {
     // while the chunk runs: analyse the jobs retired after the previous chunk
     for (Job* j : fetched) analyse(s, *j);
     fetched.clear();
-    if (!launched) {
+    const bool head_running = head && cudaEventQuery(s->head_done) == cudaErrorNotReady;
+    if (!launched && !head) {
       s->gap_open = false;  // idle for lack of work, not for the host
       // nothing resident: wait for the next arrival
       double next = 1e300;
@@ -329,29 +334,38 @@ mpc_status run_batched(mpc_server s, double deadline) {
       if (wait > 0) std::this_thread::sleep_for(std::chrono::duration<double>(std::min(wait, 0.05)));
       continue;
     }
-    // admit arrivals while the chunk runs; they join the next chunk
-    while (cudaEventQuery(s->chunk_done) == cudaErrorNotReady ||
-           (head && cudaEventQuery(s->head_done) == cudaErrorNotReady)) {
+    if (launched) {
+      // admit arrivals while the chunk runs; they join the next chunk
+      while (cudaEventQuery(s->chunk_done) == cudaErrorNotReady) {
+        admit(s);
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+      }
+      cudaGetLastError();
+      s->gap_open = true;  // the GPU is idle from here until the next chunk is enqueued
+      s->gap_from = now_s(s->t0);
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, s->chunk_start, s->chunk_done) == cudaSuccess) s->stats.gpu_ms += ms;
+      else cudaGetLastError();
+      if (mpc_status st = mpc_batch_synchronize(s->batch); st != MPC_OK)
+        return sfail(s, st, std::string("batch: ") + mpc_batch_last_error(s->batch));
+    } else if (head_running) {
+      // only the head steps: poll it, admitting arrivals meanwhile
       admit(s);
       std::this_thread::sleep_for(std::chrono::microseconds(200));
     }
     cudaGetLastError();
-    s->gap_open = true;  // the GPU is idle from here until the next chunk is enqueued
-    s->gap_from = now_s(s->t0);
-    {
-      float ms = 0.0f;
-      if (cudaEventElapsedTime(&ms, s->chunk_start, s->chunk_done) == cudaSuccess) s->stats.gpu_ms += ms;
-      else cudaGetLastError();
+    if (head && cudaEventQuery(s->head_done) == cudaSuccess) {
+      // the head finished its steps (a capacity repair, if any, completes them here)
+      if (mpc_status st = mpc_synchronize(head->h); st != MPC_OK)
+        return sfail(s, st, "head job: " + head->h->err);
+      batch_set_detached(head->h, false);
+      head->h->stream = s->stream;
+      s->head = nullptr;
     }
-    if (mpc_status st = mpc_batch_synchronize(s->batch); st != MPC_OK)
-      return sfail(s, st, std::string("batch: ") + mpc_batch_last_error(s->batch));
+    cudaGetLastError();
     for (Job& j : s->jobs) {
-      if (j.res.status != MPC_JOB_RUNNING || !j.h || j.h->target_step < j.spec.steps) continue;
-      if (&j == s->head) {
-        batch_set_detached(j.h, false);
-        j.h->stream = s->stream;
-        s->head = nullptr;
-      }
+      if (j.res.status != MPC_JOB_RUNNING || !j.h || &j == s->head || j.h->target_step < j.spec.steps)
+        continue;
       const mpc_status st = fetch(s, j);
       mpc_batch_remove(s->batch, j.h);
       j.h = nullptr;
@@ -406,6 +420,7 @@ mpc_status mpc_server_destroy(mpc_server s) {
   if (s->chunk_done) cudaEventDestroy(s->chunk_done);
   if (s->chunk_start) cudaEventDestroy(s->chunk_start);
   if (s->head_done) cudaEventDestroy(s->head_done);
+  if (s->head_ready) cudaEventDestroy(s->head_ready);
   if (s->head_stream) cudaStreamDestroy(s->head_stream);
   if (s->side) cudaStreamDestroy(s->side);
   delete s;
@@ -445,7 +460,8 @@ mpc_status mpc_server_create(const mpc_server_config* cfg, void* stream, mpc_ser
     int least = 0, greatest = 0;
     if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
         cudaStreamCreateWithPriority(&s->head_stream, cudaStreamNonBlocking, greatest) != cudaSuccess ||
-        cudaEventCreateWithFlags(&s->head_done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&s->head_done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->head_ready, cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
       mpc_server_destroy(s);
       return sfail(nullptr, MPC_ECUDA, "priority stream creation failed");

@@ -57,7 +57,7 @@ def _run(mpc, jobs, budget, **kw):
 
 @pytest.mark.parametrize("policy", [{}, {"share_all": True}, {"first_come": True},
                                     {"fill_kparticles": 1}, {"aged": True, "backfill": True},
-                                    {"priority_head": True}])
+                                    {"priority_head": True}, {"priority_head": True, "aged": True}])
 def test_each_job_same_alone_and_in_the_mix(policy):
     mpc = _mpc()
     peaks = [_peak(mpc, j)[1] for j in TRACE]
