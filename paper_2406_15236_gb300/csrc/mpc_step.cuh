@@ -1110,9 +1110,16 @@ template <int VAR>
 constexpr int kMinBlocks = VAR == 1 ? 6 : 8;
 
 // One box: one CTA per brick.  DEFER: the smaller shared-memory tile (7 CTAs per SM for
-// AT+a), bricks that exceed it left to k_step_deferred.
+// AT+a, 9 for SRD and SRD+a), bricks that exceed it left to k_step_deferred.
 template <int VAR, bool DEFER>
-constexpr int kMinBlocksStep = DEFER ? 7 : kMinBlocks<VAR>;
+constexpr int kMinBlocksStep = DEFER ? (VAR == 1 ? 7 : 9) : kMinBlocks<VAR>;
+
+// the variants and summation modes that take the deferring kernel on large boxes: AT+a
+// (7 CTAs per SM instead of 6, both modes), SRD and SRD+a with floating-point sums (9
+// instead of 8; their fixed-point kernels need more than the 56 registers a ninth CTA
+// leaves)
+template <int VAR, bool DET>
+constexpr bool kDefers = VAR == 1 || !DET;
 
 template <int VAR, bool DET, int TIER, bool DEFER = false>
 __global__ void __launch_bounds__(kThreads, kMinBlocksStep<VAR, DEFER>) k_step(const StepArgs a) {
@@ -1187,7 +1194,7 @@ template <int VAR, bool DET>
 cudaError_t set_cap_tiers(int v) {
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e = cudaFuncSetAttribute(k_step<VAR, DET, 0>, a, v);
-  if constexpr (VAR == 1) {
+  if constexpr (kDefers<VAR, DET>) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<VAR, DET, 1, true>, a, v);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<VAR, DET, 2, true>, a, v);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step_deferred<VAR, DET>, a, v);
@@ -1217,7 +1224,7 @@ size_t deferred_smem_bytes(const Geom& g) {
 template <int VAR, bool DET>
 void launch_tier(const StepArgs& a, size_t bytes, cudaStream_t s) {
   const int tier = tier_of(a.g);
-  if constexpr (VAR == 1) {
+  if constexpr (kDefers<VAR, DET>) {
     // tiers 1 and 2 (16-bit tags) fit 7 CTAs per SM with the smaller tile; tier 3's 128
     // cells do not
     if ((tier == 1 || tier == 2) && a.g.nbricks >= kDeferMinBricks && a.deferred) {

@@ -1,8 +1,9 @@
-"""The deferring step kernel of large MPC-AT+a boxes.
+"""The deferring step kernel of large boxes.
 
 Boxes of 8192 bricks or more step with a kernel whose shared-memory tile holds 736 of a
-brick's 864 slots (7 CTAs per SM instead of 6); a brick that holds more particles in a
-step is left to a full-capacity pass launched right after it.  At uniform density that
+brick's 864 slots (7 CTAs per SM instead of 6 for MPC-AT+a, 9 instead of 8 for SRD and
+MPC-SRD+a); a brick that holds more particles in a step is left to a full-capacity pass
+launched right after it.  At uniform density that
 is ~7e-5 of the bricks.  Here a 128^3 box (32,768 bricks of 4^3 cells) gets a denser slab
 (N_c 11.5 in x < 32, so about half of that slab's bricks exceed the tile) by moving
 particles into it with set_state.  For two consecutive steps, particles of cells sampled
@@ -46,13 +47,15 @@ def _neighbourhood(X, F, cells):
     return mark[ucell]
 
 
-def test_deferred_bricks_match_oracle():
+@pytest.mark.parametrize("variant,h", [(1, 0.05), (0, 0.1), (2, 0.05)])
+def test_deferred_bricks_match_oracle(variant, h):
     import torch
 
     import paper_2406_15236_gb300 as mpc
 
     torch.cuda.set_device(0)
-    sim = mpc.Simulation(flags=mpc.MPC_FLAG_OBSERVABLES, **KW)
+    kw = dict(KW, variant=variant, h=h)
+    sim = mpc.Simulation(flags=mpc.MPC_FLAG_OBSERVABLES, **kw)
     N = sim.N
     F = sim.info.fixed_bits
     nb = sim.info.n_bricks
@@ -66,7 +69,7 @@ def test_deferred_bricks_match_oracle():
         np.stack([rng.integers(2, L // 4 - 2, 40), rng.integers(0, L, 40), rng.integers(0, L, 40)], axis=1),
         np.stack([rng.integers(L // 2, L, 10), rng.integers(0, L, 10), rng.integers(0, L, 10)], axis=1)])
     sampled = set(int(cx + L * (cy + L * cz)) for cx, cy, cz in cells)
-    p = par.oracle_params(**KW)
+    p = par.oracle_params(**kw)
     for k in range(2):
         X0, V0, id0, s0 = sim.get_state()
         assert X0.shape[1] == N and int(id0.astype(np.int64).sum()) == N * (N - 1) // 2
