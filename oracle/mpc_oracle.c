@@ -10,8 +10,14 @@
  *
  * Parity pins (tests/test_oracle_*.py): Philox against cuRAND's host generator; the
  * rotation against scipy's Rotation; cell assignment against exact rational
- * enumeration; conservation laws; sampler distributions against scipy.stats;
- * equipartition; Poiseuille flow against its closed form.
+ * enumeration; streaming and wall reflections against their closed forms; conservation
+ * laws; sampler distributions against scipy.stats; equipartition; Poiseuille flow
+ * against its closed form; the angular-momentum solve against numpy's solve / pinv and
+ * its float32 sensitivity against float32 evaluations; the ill-conditioning flag against
+ * LAPACK eigenvalues; phantom particles (counts, aggregate momentum and energy, one-by-one
+ * positions and velocities) against their distributions and an independent numpy
+ * collision; the stress observables against the momentum flux through planes, and their
+ * Green-Kubo viscosity against the SRD closed form.  Every function here has a pin.
  */
 #include "mpc_oracle.h"
 
