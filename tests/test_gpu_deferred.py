@@ -129,3 +129,42 @@ def test_deterministic_deferred_equals_full_tile():
     assert np.array_equal(results[0][0], results[1][0])
     assert np.array_equal(results[0][1].view(np.uint32), results[1][1].view(np.uint32))
     assert np.array_equal(results[0][3], results[1][3])
+
+
+def test_deferred_solo_member_of_a_batch_equals_packed():
+    """A large member of a batch steps alone with the deferring kernel (and its
+    full-capacity pass) inside the batch's graph; in the fixed-point mode its trajectory
+    must equal the same member packed with the others (the packed kernel, full tile)."""
+    import torch
+
+    import paper_2406_15236_gb300 as mpc
+
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(8)
+    small = dict(L=12, n_c=10.0, h=0.1, variant=0, seed=31)
+    state0 = None
+    results = []
+    for pack_all in (False, True):
+        with mpc.Batch(deterministic=True, graph_steps=4, pack_all=pack_all) as b:
+            big = b.add(**KW)
+            other = b.add(**small)
+            if state0 is None:
+                X, V, ids, s = big.get_state()
+                state0 = (_dense_slab_state(X, big.info.fixed_bits, rng), V, ids, s)
+            big.set_state(*state0)
+            b.step(6)
+            assert b.info().solo_boxes == (0 if pack_all else 1)
+            X, V, ids, s = big.get_state()
+            o = np.argsort(ids)
+            results.append((X[:, o], V[:, o].view(np.uint32), s, _state_of(other)))
+    assert results[0][2] == results[1][2] == 6
+    assert np.array_equal(results[0][0], results[1][0])
+    assert np.array_equal(results[0][1], results[1][1])
+    for a, c in zip(results[0][3], results[1][3]):
+        assert np.array_equal(a, c)
+
+
+def _state_of(box):
+    X, V, ids, _ = box.get_state()
+    o = np.argsort(ids)
+    return X[:, o], V[:, o].view(np.uint32)
