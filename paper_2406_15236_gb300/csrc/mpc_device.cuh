@@ -268,6 +268,23 @@ __device__ __forceinline__ void stream(const Geom& g, uint32_t& x, uint32_t& y, 
   y = add_wrap(y, dy, g.P[1]);
 }
 
+// stream() for a periodic box without gravity whose extents P are powers of two (the
+// displacement clamped to +-(P - 1) as there; (x + d) mod P is then a mask): the same
+// result in fewer instructions.
+__device__ __forceinline__ void stream_periodic_pow2(const Geom& g, uint32_t& x, uint32_t& y, uint32_t& z,
+                                                     float vx, float vy, float vz) {
+  x = (x + (uint32_t)displacement(vx, g.hs, g.P[0])) & (g.P[0] - 1u);
+  y = (y + (uint32_t)displacement(vy, g.hs, g.P[1])) & (g.P[1] - 1u);
+  z = (z + (uint32_t)displacement(vz, g.hs, g.P[2])) & (g.P[2] - 1u);
+}
+
+// the boxes stream_periodic_pow2 serves
+__host__ __device__ inline bool periodic_pow2_box(const Geom& g) {
+  bool ok = g.walls == 0 && g.gh[0] == 0.0f && g.gh[1] == 0.0f && g.gh[2] == 0.0f;
+  for (int ax = 0; ax < 3; ++ax) ok = ok && (g.P[ax] & (g.P[ax] - 1u)) == 0u;
+  return ok;
+}
+
 // The exact inverse of stream(): from a stored (streamed) position and the velocity v it
 // was streamed with (before the kick), the position before the step.
 __device__ __forceinline__ void unstream(const Geom& g, uint32_t& x, uint32_t& y, uint32_t& z,

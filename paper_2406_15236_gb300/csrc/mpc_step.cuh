@@ -16,7 +16,7 @@
 //      about the cell's centre of mass,
 //   4. applies the collision to every particle, streams it for step n+1 (its only
 //      streaming per step), finds the brick of its next collision cell and ranks it
-//      within its warp's group for that destination (warp-aggregated shared atomics),
+//      within its warp's group for that destination (shared-memory atomics),
 //   5. per warp, without a block barrier (a thread writes out the particles it
 //      collided): reserves the warp's run in each destination with one global atomic
 //      and writes its particles out in contiguous runs, the ids read again from the
@@ -358,14 +358,18 @@ __device__ __forceinline__ float3 solve_omega(int n, float Mxx, float Myy, float
 // sh.bar once and tracks its phase (persistent kernels); otherwise the barrier is
 // initialised here and phase must be 0.  DEFER (TIER > 0): the shared-memory tile holds
 // T::scap particles, and a brick holding more is appended to a.deferred and left
-// untouched (its count slot too) for the full-capacity pass.  Returns false after a
-// bounded wait gave up (the CTA must stop).
-template <int VAR, bool DET, bool PERSIST, int TIER = 0, bool DEFER = false>
+// untouched (its count slot too) for the full-capacity pass.  PLAIN: the box is periodic,
+// without gravity, with power-of-two extents (periodic_pow2_box): the kick, the wall
+// handling and the general wrap are compiled out (5 % of the AT+a and SRD step).
+// Returns false after a bounded wait gave up (the CTA must stop).
+template <int VAR, bool DET, bool PERSIST, int TIER = 0, bool DEFER = false, bool PLAIN = false>
 __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsigned char* smem,
                                            BrickShared& sh, uint32_t& phase) {
   const Geom& g = a.g;
   using T = TierShape<TIER>;
   static_assert(!DEFER || TIER > 0, "deferral needs a compiled-in brick tier");
+  // the compiled-in tiers serve no debug boxes (tier_of), so their debug paths compile out
+  const bool debug = TIER == 0 && g.debug;
   // brick geometry: compile-time constants for TIER > 0, else from the Geom
   const int cap = TIER ? T::cap : g.cap;
   // particles the shared-memory tile holds (the global brick slots hold cap)
@@ -499,7 +503,7 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
     const uint32_t zraw = sz[i];
     const uint32_t x = sx[i], y = sy[i], z = zraw & ~kCrossedBit;
     float vx = svx[i], vy = svy[i], vz = svz[i];
-    collision_velocity(g, zraw, vx, vy, vz);
+    if constexpr (!PLAIN) collision_velocity(g, zraw, vx, vy, vz);
     int cx = 0, cy = 0, cz = 0, lx, ly, lz;
     if (inner) {
       lx = (int)(x + S0x - Ox) >> g.F;
@@ -517,7 +521,7 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
     const uint32_t lcr = in ? (lc | (rank << kCellBits)) : kNoCell;
     binerr |= !in;
     stag[i] = (Tag)lcr;
-    if (g.debug) sgc[i] = (uint32_t)cx + (uint32_t)g.Lc[0] * ((uint32_t)cy + (uint32_t)g.Lc[1] * (uint32_t)cz);
+    if (debug) sgc[i] = (uint32_t)cx + (uint32_t)g.Lc[0] * ((uint32_t)cy + (uint32_t)g.Lc[1] * (uint32_t)cz);
     if constexpr (VAR == 1) {
       // AT+a: keep v_ran and w = v - v_ran
       const float3 u = normal3_at(draw(g, sid[i], step, kTagAtVel, 0u), g.sigma);
@@ -574,7 +578,7 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
       const uint32_t cg = (uint32_t)cx + (uint32_t)g.Lc[0] * ((uint32_t)cy + (uint32_t)g.Lc[1] * (uint32_t)cz);
       const int n = exists ? (int)scount[lc] : 0;
       const int base = exists ? (int)scstart[lc] : 0;
-      if (exists && sub == 0 && g.debug) a.dbg_counts[cg] = (uint32_t)n;
+      if (exists && sub == 0 && debug) a.dbg_counts[cg] = (uint32_t)n;
       if constexpr (VAR == 0) {
         float s0 = 0.f, s1 = 0.f, s2 = 0.f;
         if constexpr (DET) {
@@ -598,7 +602,7 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
         // (Sec. II, Boundary conditions): Poisson count, Gaussian total momentum, and
         // an internal kinetic energy ~ kT chi^2(3(n_ph - 1)); drawn by the group leader
         float nph = 0.f, Px = 0.f, Py = 0.f, Pz = 0.f, Kint = 0.f;
-        if (exists && n > 0 && sub == 0 && g.walls == 1 && (cz == 0 || cz == g.L[2])) {
+        if (!PLAIN && exists && n > 0 && sub == 0 && g.walls == 1 && (cz == 0 || cz == g.L[2])) {
           const double sz_ = (double)S0z * (double)g.inv2F;
           const double phi = (cz == 0) ? sz_ : 1.0 - sz_;
           const uint4 r = draw(g, cg, step, kTagPhantom, 0u);
@@ -867,7 +871,7 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
 #pragma unroll
     for (int q = 0; q < 13; ++q) o_q[q] = 0;
   }
-  const bool zper = !g.walls;
+  const bool zper = PLAIN || !g.walls;
   for (int i = tid; i < cnt; i += kThreads) {
     uint32_t x = sx[i], y = sy[i], z = sz[i] & ~kCrossedBit;
     float vbx = svx[i], vby = svy[i], vbz = svz[i];  // AT+a: w
@@ -932,7 +936,8 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
     }
     // stream for step n+1 (this is the only streaming of the particle per step) and
     // find the brick of its next collision cell
-    stream(g, x, y, z, nx, ny, nz);
+    if constexpr (PLAIN) stream_periodic_pow2(g, x, y, z, nx, ny, nz);
+    else stream(g, x, y, z, nx, ny, nz);
     sx[i] = x; sy[i] = y; sz[i] = z;
     svx[i] = nx; svy[i] = ny; svz[i] = nz;
     const uint32_t zs = z & ~kCrossedBit;
@@ -955,15 +960,23 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
                  ? 27u
                  : (uint32_t)((dxb + 1) + 3 * (dyb + 1) + 9 * (dzb + 1));
     }
-    // rank within the destination group: the lanes of a warp bound for the same group
-    // (most of them stay in this brick) get consecutive slots from one shared-memory
-    // atomic by the first of them, so their writes below are contiguous runs
-    const uint32_t active = __activemask();
-    const uint32_t peers = __match_any_sync(active, code);
-    const int leader = __ffs(peers) - 1;
-    uint32_t rank0 = 0;
-    if (lane == leader) rank0 = atomicAdd(&wcount[28 * (tid >> 5) + code], (uint32_t)__popc(peers));
-    const uint32_t rank = __shfl_sync(active, rank0, leader) + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+    // rank within the warp's group for the destination: the lanes bound for the same
+    // brick take distinct slots of one run, so their writes below are contiguous.  AT+a:
+    // one shared-memory atomic per lane on the warp's counter (0.6 warp instructions per
+    // particle fewer than grouping first, 0.8 % faster); SRD and SRD+a, with 9 CTAs per SM
+    // contending for the atomic unit: the lanes grouped by destination (match) and one
+    // atomic per group (1.8 % faster there)
+    uint32_t rank;
+    if constexpr (VAR == 1) {
+      rank = atomicAdd(&wcount[28 * (tid >> 5) + code], 1u);
+    } else {
+      const uint32_t active = __activemask();
+      const uint32_t peers = __match_any_sync(active, code);
+      const int leader = __ffs(peers) - 1;
+      uint32_t rank0 = 0;
+      if (lane == leader) rank0 = atomicAdd(&wcount[28 * (tid >> 5) + code], (uint32_t)__popc(peers));
+      rank = __shfl_sync(active, rank0, leader) + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+    }
     stag[i] = (Tag)(code | (rank << 5));
   }
   // ---- 5. per warp: this warp's runs in the destination bricks (one global atomic per
@@ -1028,7 +1041,7 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
         dX[o] = sx[i]; dY[o] = sy[i]; dZ[o] = sz[i];
         dVX[o] = svx[i]; dVY[o] = svy[i]; dVZ[o] = svz[i];
         dID[o] = id;
-        if (g.debug) dst.cell[o] = sgc[i];
+        if (debug) dst.cell[o] = sgc[i];
       } else {
         rare = true;
       }
@@ -1082,7 +1095,7 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
         dX[o] = sx[i]; dY[o] = sy[i]; dZ[o] = sz[i];
         dVX[o] = svx[i]; dVY[o] = svy[i]; dVZ[o] = svz[i];
         dID[o] = id;
-        if (g.debug) dst.cell[o] = sgc[i];
+        if (debug) dst.cell[o] = sgc[i];
       } else {
         atomicExch(&a.ctrl->overflow, 1);
         const uint32_t s = atomicAdd(&a.ctrl->spill_count, 1u);
@@ -1090,7 +1103,7 @@ __device__ __forceinline__ bool step_brick(const StepArgs& a, const int b, unsig
           a.spill.x[0][s] = sx[i]; a.spill.x[1][s] = sy[i]; a.spill.x[2][s] = sz[i];
           a.spill.v[0][s] = svx[i]; a.spill.v[1][s] = svy[i]; a.spill.v[2][s] = svz[i];
           a.spill.id[s] = id;
-          if (g.debug) a.spill.cell[s] = sgc[i];
+          if (debug) a.spill.cell[s] = sgc[i];
           a.spill.dest[s] = d;
         } else {
           atomicExch(&a.ctrl->lost, 1);
@@ -1121,12 +1134,12 @@ constexpr int kMinBlocksStep = DEFER ? (VAR == 1 ? 7 : 9) : kMinBlocks<VAR>;
 template <int VAR, bool DET>
 constexpr bool kDefers = VAR == 1 || !DET;
 
-template <int VAR, bool DET, int TIER, bool DEFER = false>
+template <int VAR, bool DET, int TIER, bool DEFER = false, bool PLAIN = false>
 __global__ void __launch_bounds__(kThreads, kMinBlocksStep<VAR, DEFER>) k_step(const StepArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ BrickShared sh;
   uint32_t phase = 0;
-  step_brick<VAR, DET, false, TIER, DEFER>(a, blockIdx.x, smem, sh, phase);
+  step_brick<VAR, DET, false, TIER, DEFER, PLAIN>(a, blockIdx.x, smem, sh, phase);
 }
 
 // The full-capacity pass of a step: the bricks a deferring k_step left in a.deferred, by
@@ -1197,6 +1210,8 @@ cudaError_t set_cap_tiers(int v) {
   if constexpr (kDefers<VAR, DET>) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<VAR, DET, 1, true>, a, v);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<VAR, DET, 2, true>, a, v);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<VAR, DET, 1, true, true>, a, v);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<VAR, DET, 2, true, true>, a, v);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step_deferred<VAR, DET>, a, v);
   }
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<VAR, DET, 1>, a, v);
@@ -1230,8 +1245,14 @@ void launch_tier(const StepArgs& a, size_t bytes, cudaStream_t s) {
     if ((tier == 1 || tier == 2) && a.g.nbricks >= kDeferMinBricks && a.deferred) {
       const size_t tile = make_layout(TierShape<1>::scap, a.g.brick_cells, CellParams<VAR>::kParams,
                                       CellParams<VAR>::kStoresRandomVelocity, 0, 2).total;
-      if (tier == 1) k_step<VAR, DET, 1, true><<<a.g.nbricks, kThreads, tile, s>>>(a);
-      else k_step<VAR, DET, 2, true><<<a.g.nbricks, kThreads, tile, s>>>(a);
+      // periodic, gravity-free boxes of power-of-two extents take the plain body
+      if (periodic_pow2_box(a.g)) {
+        if (tier == 1) k_step<VAR, DET, 1, true, true><<<a.g.nbricks, kThreads, tile, s>>>(a);
+        else k_step<VAR, DET, 2, true, true><<<a.g.nbricks, kThreads, tile, s>>>(a);
+      } else {
+        if (tier == 1) k_step<VAR, DET, 1, true><<<a.g.nbricks, kThreads, tile, s>>>(a);
+        else k_step<VAR, DET, 2, true><<<a.g.nbricks, kThreads, tile, s>>>(a);
+      }
       k_step_deferred<VAR, DET><<<kDeferGrid, kThreads, deferred_smem_bytes<VAR>(a.g), s>>>(a);
       return;
     }

@@ -5,8 +5,8 @@ brick's 864 slots (7 CTAs per SM instead of 6 for MPC-AT+a, 9 instead of 8 for S
 MPC-SRD+a); a brick that holds more particles in a step is left to a full-capacity pass
 launched right after it.  At uniform density that
 is ~7e-5 of the bricks.  Here a 128^3 box (32,768 bricks of 4^3 cells) gets a denser slab
-(N_c 11.5 in x < 32, so about half of that slab's bricks exceed the tile) by moving
-particles into it with set_state.  For two consecutive steps, particles of cells sampled
+(N_c 11 in x < 32: about a tenth of that slab's bricks exceed the tile in a step, and
+none comes near the 864 slots of a brick) by moving particles into it with set_state.  For two consecutive steps, particles of cells sampled
 inside the slab and outside it are compared with the oracle (stepped on the neighbourhood
 of each sampled cell: the particles that collide in cell c come from unshifted cells
 c-2..c+1 per axis); the second step also shows that the list of deferred bricks was
@@ -27,17 +27,19 @@ L = 128
 KW = dict(L=L, n_c=10.0, h=0.05, kT=1.0, variant=1, seed=11)
 
 
-def _dense_slab_state(X, F, rng):
-    """moves 7.5 % of the particles of x >= L/2 to uniform positions in x < L/4: the
-    slab's density becomes 10 (1 + 0.075 * 2) = 11.5 per cell"""
-    src = np.nonzero((X[0] >> F) >= L // 2)[0]
-    pick = rng.choice(src, size=int(0.075 * src.size), replace=False)
+def _dense_slab_state(X, ids, F, rng, L=L):
+    """moves 5 % of the particles of x >= L/2 (chosen by id, so that the state does not
+    depend on the order get_state returns them in) to uniform positions in x < L/4: the
+    slab's density becomes 10 (1 + 0.05 * 2) = 11 per cell"""
+    by_id = np.argsort(ids)
+    src = by_id[(X[0, by_id] >> F) >= L // 2]
+    pick = rng.choice(src, size=int(0.05 * src.size), replace=False)
     X = X.copy()
     X[0, pick] = rng.integers(0, (L // 4) << F, size=pick.size, dtype=np.uint64).astype(np.uint32)
     return X
 
 
-def _neighbourhood(X, F, cells):
+def _neighbourhood(X, F, cells, L=L):
     ucell = (X[0] >> F).astype(np.int64) + L * ((X[1] >> F).astype(np.int64) + L * (X[2] >> F).astype(np.int64))
     mark = np.zeros(L ** 3, dtype=bool)
     offs = np.arange(-2, 2)
@@ -47,14 +49,16 @@ def _neighbourhood(X, F, cells):
     return mark[ucell]
 
 
-@pytest.mark.parametrize("variant,h", [(1, 0.05), (0, 0.1), (2, 0.05)])
-def test_deferred_bricks_match_oracle(variant, h):
+# L = 128: a periodic box of power-of-two extent without gravity (the plain kernel body);
+# L = 96: the general streaming body with the deferring kernel
+@pytest.mark.parametrize("variant,h,L", [(1, 0.05, 128), (0, 0.1, 128), (2, 0.05, 128), (1, 0.05, 96)])
+def test_deferred_bricks_match_oracle(variant, h, L):
     import torch
 
     import paper_2406_15236_gb300 as mpc
 
     torch.cuda.set_device(0)
-    kw = dict(KW, variant=variant, h=h)
+    kw = dict(KW, variant=variant, h=h, L=L)
     sim = mpc.Simulation(flags=mpc.MPC_FLAG_OBSERVABLES, **kw)
     N = sim.N
     F = sim.info.fixed_bits
@@ -62,7 +66,7 @@ def test_deferred_bricks_match_oracle(variant, h):
     assert nb[0] * nb[1] * nb[2] >= 8192
     rng = np.random.default_rng(5)
     X, V, ids, s = sim.get_state()
-    X = _dense_slab_state(X, F, rng)
+    X = _dense_slab_state(X, ids, F, rng, L)
     sim.set_state(X, V, ids, s)
     # cells inside the dense slab (most of them in deferred bricks) and outside it
     cells = np.concatenate([
@@ -73,7 +77,7 @@ def test_deferred_bricks_match_oracle(variant, h):
     for k in range(2):
         X0, V0, id0, s0 = sim.get_state()
         assert X0.shape[1] == N and int(id0.astype(np.int64).sum()) == N * (N - 1) // 2
-        sel = _neighbourhood(X0, F, cells)
+        sel = _neighbourhood(X0, F, cells, L)
         Xs, Vs, idss = X0[:, sel], V0[:, sel], id0[sel]
         sim.step(1)
         X1, V1, id1, s1 = sim.get_state()
@@ -115,7 +119,7 @@ def test_deterministic_deferred_equals_full_tile():
         if tile == 640:
             assert nb[0] * nb[1] * nb[2] >= 8192 and sim.info.capacity == 864  # deferring kernel
             X, V, ids, s = sim.get_state()
-            state0 = (_dense_slab_state(X, sim.info.fixed_bits, rng), V, ids, s)
+            state0 = (_dense_slab_state(X, ids, sim.info.fixed_bits, rng), V, ids, s)
         else:
             assert sim.info.capacity != 864  # the generic kernel
         sim.set_state(*state0)
@@ -150,7 +154,7 @@ def test_deferred_solo_member_of_a_batch_equals_packed():
             other = b.add(**small)
             if state0 is None:
                 X, V, ids, s = big.get_state()
-                state0 = (_dense_slab_state(X, big.info.fixed_bits, rng), V, ids, s)
+                state0 = (_dense_slab_state(X, ids, big.info.fixed_bits, rng), V, ids, s)
             big.set_state(*state0)
             b.step(6)
             assert b.info().solo_boxes == (0 if pack_all else 1)
